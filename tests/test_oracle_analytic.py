@@ -1,0 +1,155 @@
+"""Pins of the oracle against closed forms and the paper's printed numbers.
+
+* Eq. 61: the melting root reproduces the interface position the paper prints.
+* Eq. 60-61: 1D melting of a half-space (the 64x4x4 conduction workload).
+* Eq. 62-63: 1D solidification, Sec. 3.1.2 case (a).
+* Eq. 20 / Eq. 34: the decay rate of a sinusoidal conduction mode gives back the
+  diffusivity fixed by the relaxation time.
+* Eq. 47 (Sec. 2.4): with sigma_1 + sigma_4 = 2 the solid ahead of the front stays
+  exactly at h_m; otherwise it does not; SRT with tau far from 1 cools the solid.
+* Steady conduction between isothermal walls gives Nu = 1.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import lbpc_inputs as inp
+import oracle
+from oracle import neumann as nm
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_melting_root_reproduces_printed_front():
+    rows = np.loadtxt(os.path.join(GOLDEN, "neumann_melting_front.txt"), ndmin=2)
+    for chi, ste, t, X in rows:
+        k = nm.melting_k(ste)
+        assert abs(float(nm.melting_front(t, chi, k)) - X) < 5e-4
+        # the root satisfies Eq. 61 itself
+        assert abs(ste / (math.exp(k * k) * math.erf(k)) - k * math.sqrt(math.pi)) < 1e-12
+
+
+def test_solidification_root_case_a():
+    # equal properties: Ste_s = Ste_l = 0.004, chi_s = chi_l
+    k = nm.solidification_k(0.004, 0.004, 0.4, 0.4)
+    # small-k limit of Eq. 63 with equal properties: Ste/(k sqrt(pi)) ... solved exactly
+    lhs = 0.004 / (math.exp(k * k) * math.erf(k)) - 0.004 / (math.exp(k * k) * math.erfc(k))
+    assert abs(lhs - k * math.sqrt(math.pi)) < 1e-12
+    assert 0.043 < k < 0.044
+
+
+@pytest.mark.parametrize("enth_model,tol", [(inp.ENTH_MRT, 0.01), (inp.ENTH_SRT, 0.03)])
+def test_stefan_melting_front_and_profile(enth_model, tol):
+    """64x4x4, St = 0.1, tau_g = 0.8 (chi = 0.075), 5000 steps, hot wall at x = -1/2."""
+    w = inp.stefan_melting(enth_model=enth_model)
+    o = oracle.run(w)
+    lat = o.lattice()
+    assert np.isclose(lat["chi"], 0.075)
+    k = nm.melting_k(0.1)
+    X = float(nm.melting_front(w.steps, lat["chi"], k))
+    d = o.diagnostics()
+    assert abs(d["front_mean"] - X) / X < tol
+    F = o.fields()
+    T = F["T"][0, 0, :]
+    x = np.arange(w.shape[0]) + 0.5
+    Ta = nm.melting_temperature(x, w.steps, lat["chi"], k)
+    liquid = F["fl"][0, 0, :] == 1.0
+    assert np.abs(T[liquid] - Ta[liquid]).max() < (0.01 if enth_model == inp.ENTH_MRT else 0.03)
+    # uniform in y and z
+    assert np.abs(F["T"] - F["T"][:1, :1, :]).max() < 1e-14
+
+
+def test_stefan_solidification_case_a():
+    """Sec. 3.1.2 case (a): chi = 0.4, Ste = 0.004, liquid at T0 = 1, wall at T1 = -1."""
+    w = inp.stefan_solidification(nx=160)
+    o = oracle.run(w)
+    lat = o.lattice()
+    assert np.isclose(lat["chi"], 0.4)
+    k = nm.solidification_k(0.004, 0.004, 0.4, 0.4)
+    t = w.steps
+    X = float(nm.solidification_front(t, 0.4, k))
+    F = o.fields()
+    solid_depth = (1.0 - F["fl"][0, 0, :]).sum()
+    assert abs(solid_depth - X) / X < 0.03
+    x = np.arange(w.shape[0]) + 0.5
+    Ta = nm.solidification_temperature(x, t, 0.4, 0.4, k)
+    assert np.abs(F["T"][0, 0, :] - Ta).max() < 0.01
+
+
+def _decay_rate(nx, params, t1=300, t2=900):
+    o = oracle.Oracle((nx, 1, 1), params)
+    L = o.lattice()["latent"]
+    x = np.arange(nx)
+    amp = 0.1
+    o.set_initial_h(L + 1.0 + amp * np.sin(2 * np.pi * x / nx))  # all liquid
+    o.step(t1)
+    a1 = abs(np.fft.rfft(o.fields()["T"][0, 0, :])[1])
+    o.step(t2 - t1)
+    a2 = abs(np.fft.rfft(o.fields()["T"][0, 0, :])[1])
+    return math.log(a1 / a2) / (t2 - t1), o.lattice()["chi"]
+
+
+@pytest.mark.parametrize("enth_model,tau", [(inp.ENTH_SRT, 0.6), (inp.ENTH_SRT, 0.8),
+                                            (inp.ENTH_SRT, 1.5), (inp.ENTH_MRT, 0.6),
+                                            (inp.ENTH_MRT, 0.9), (inp.ENTH_MRT, 1.4)])
+def test_sine_mode_decay_gives_the_diffusivity(enth_model, tau):
+    """Eq. 20 (SRT) and Eq. 34 (MRT): a periodic sine mode of T decays at chi k^2 to
+    leading order; Richardson extrapolation of r/k^2 over two wavelengths removes
+    the O(k^2) lattice correction."""
+    p = inp.Params(flow_model=0, enth_model=enth_model, tau_g=tau, bc=[inp.PERIODIC] * 6,
+                   St=1.0)
+    r1, chi = _decay_rate(32, p)
+    r2, _ = _decay_rate(64, p, t1=600, t2=2600)
+    R1, R2 = r1 / (2 * np.pi / 32) ** 2, r2 / (2 * np.pi / 64) ** 2
+    chi_ext = (4 * R2 - R1) / 3
+    assert np.isclose(chi, (tau - 0.5) * 0.25)
+    assert abs(R2 - chi) / chi < 0.02
+    assert abs(chi_ext - chi) / chi < 1e-3
+
+
+def _solid_ahead_error(w, steps):
+    o = oracle.run(w, steps=steps)
+    F = o.fields()
+    fl = F["fl"][0, 0, :]
+    h = F["h"][0, 0, :]
+    front = int(np.argmax(fl < 1.0))  # first not fully liquid node
+    return np.abs(h[front + 2:] - 0.0).max(), F["T"][0, 0, front + 2:].min()
+
+
+def test_relaxation_rule_keeps_solid_at_melting_enthalpy():
+    """Eq. 47: sigma_1 + sigma_4 = 2 keeps every node two cells ahead of the front at h_m."""
+    w = inp.stefan_melting(enth_model=inp.ENTH_MRT, tau_g=1 / 1.14)
+    err, _ = _solid_ahead_error(w, 3000)
+    assert err <= 1e-13
+    # case (c) of Sec. 3.1.2: sigma_4 = sigma_5 = 1.9 != 2 - sigma_1 leaks into the solid
+    wc = inp.stefan_melting(enth_model=inp.ENTH_MRT, tau_g=1 / 1.14, sigma4=1.9)
+    err_c, _ = _solid_ahead_error(wc, 3000)
+    assert err_c > 1e-6
+
+
+def test_srt_far_from_unit_tau_cools_the_solid():
+    """Sec. 3.1.1: SRT with tau = 0.564 gives a solid temperature below T_m (the paper
+    reports -0.00152 on its own grid); tau = 1 keeps the solid at T_m."""
+    w = inp.stefan_melting(enth_model=inp.ENTH_SRT, tau_g=0.564)
+    _, Tmin = _solid_ahead_error(w, 3000)
+    assert Tmin < -1e-4
+    w1 = inp.stefan_melting(enth_model=inp.ENTH_SRT, tau_g=1.0)
+    err1, _ = _solid_ahead_error(w1, 3000)
+    assert err1 <= 1e-13
+
+
+@pytest.mark.parametrize("enth_model", [inp.ENTH_SRT, inp.ENTH_MRT])
+def test_steady_conduction_nusselt_is_one(enth_model):
+    p = inp.Params(flow_model=0, enth_model=enth_model, tau_g=1.3,
+                   bc=[inp.ISOTHERMAL, inp.ISOTHERMAL] + [inp.PERIODIC] * 4,
+                   T_wall=[1.0, 0.0, 0, 0, 0, 0], St=1.0)
+    o = oracle.Oracle((16, 1, 1), p)
+    L = o.lattice()["latent"]
+    o.set_initial_h(np.full(o.N, L + 0.5))
+    o.step(12000)
+    d = o.diagnostics()
+    assert abs(d["nu_hot"] - 1.0) < 1e-9
+    T = o.fields()["T"][0, 0, :]
+    assert np.allclose(T, 1.0 - (np.arange(16) + 0.5) / 16, atol=1e-9)
