@@ -1,0 +1,133 @@
+// lbpc_host.h -- validation of the parameter block and its mapping to lattice units
+// (Eq. 20, 34, 52, 59, 64), and the kernel argument block built from it.
+#pragma once
+
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "lbpc.h"
+#include "lbpc_internal.h"
+
+namespace lbpc {
+
+struct Derived {
+    double dT, L, hs, hl, H, chi, nu, gbeta, U0;
+    double tau_g, sigma_chi, sigma4, tau_f, s_nu, s_e, s_eps, s_q, s_pi, s_t;
+};
+
+inline bool validate_and_map(int nx, int ny, int nz, const lbpc_params* p, Derived& d, std::string& e) {
+    if (!p) { e = "null parameter block"; return false; }
+    if (nx < 1 || ny < 1 || nz < 1) { e = "lattice extents must be >= 1"; return false; }
+    if ((long long)nx * ny * nz >= (1LL << 31)) { e = "lattice exceeds 2^31 - 1 nodes"; return false; }
+    if (p->flow_model < LBPC_FLOW_NONE || p->flow_model > LBPC_FLOW_SRT) { e = "flow_model must be 0, 1 or 2"; return false; }
+    if (p->enth_model != LBPC_ENTH_MRT && p->enth_model != LBPC_ENTH_SRT) { e = "enth_model must be 1 or 2"; return false; }
+    if (p->precision < LBPC_FP64 || p->precision > LBPC_BF16S) { e = "precision must be 0..3"; return false; }
+    if (p->streaming != LBPC_PULL && p->streaming != LBPC_AA) { e = "streaming must be 0 or 1"; return false; }
+    for (int f = 0; f < 6; f++)
+        if (p->bc[f] < LBPC_PERIODIC || p->bc[f] > LBPC_ADIABATIC) { e = "bc codes must be 0..2"; return false; }
+    for (int ax = 0; ax < 3; ax++)
+        if ((p->bc[2 * ax] == LBPC_PERIODIC) != (p->bc[2 * ax + 1] == LBPC_PERIODIC)) {
+            e = "periodic faces must come in pairs"; return false;
+        }
+    if (p->report_every < 0) { e = "report_every must be >= 0"; return false; }
+    if (!(p->omega_T > 0.0 && p->omega_T <= 1.0 / 3.0)) { e = "omega_T must lie in (0, 1/3]"; return false; }
+    if (!(p->Cp_s > 0 && p->Cp_l > 0 && p->Cp_ref > 0)) { e = "specific heats must be > 0"; return false; }
+    if (!(p->St > 0)) { e = "St must be > 0"; return false; }
+    d.dT = p->Th - p->Tm;
+    if (!(d.dT > 0)) { e = "Th must exceed Tm"; return false; }
+    // Stefan number (Eq. 64) fixes the latent heat; Eq. 2 with h0 = 0 gives h_s and h_l.
+    d.L = p->Cp_l * d.dT / p->St;
+    d.hs = p->Cp_s * p->Tm;
+    d.hl = d.hs + d.L;
+    d.H = (double)nx;
+    d.chi = d.nu = d.gbeta = d.U0 = 0.0;
+    if (p->flow_model != LBPC_FLOW_NONE) {
+        if (!(p->Ra > 0 && p->Pr > 0)) { e = "Ra and Pr must be > 0"; return false; }
+        if (!(p->Ma > 0 && p->Ma < 1)) { e = "Ma must lie in (0, 1)"; return false; }
+        // free-fall velocity U0 = sqrt(g beta dT H) = Ma c_s, c_s^2 = 1/3
+        d.U0 = p->Ma / std::sqrt(3.0);
+        d.nu = p->nu > 0 ? p->nu : d.U0 * d.H * std::sqrt(p->Pr / p->Ra);
+        d.chi = d.nu / p->Pr;
+        d.gbeta = d.U0 * d.U0 / (d.dT * d.H);
+    }
+    if (p->tau_g > 0) {
+        if (!(p->tau_g > 0.5)) { e = "tau_g must exceed 1/2"; return false; }
+        d.chi = (p->tau_g - 0.5) * p->omega_T;  // Eq. 20
+    }
+    if (!(d.chi > 0)) { e = "no thermal diffusivity: give tau_g > 1/2 or a flow model"; return false; }
+    d.tau_g = d.chi / p->omega_T + 0.5;  // Eq. 20 / Eq. 34 solved for the relaxation time
+    d.sigma_chi = 1.0 / d.tau_g;
+    d.sigma4 = p->enth_model == LBPC_ENTH_MRT ? (p->sigma4 > 0 ? p->sigma4 : 2.0 - d.sigma_chi)
+                                              : d.sigma_chi;  // Eq. 47
+    d.tau_f = d.s_nu = d.s_e = d.s_eps = d.s_q = d.s_pi = d.s_t = 0.0;
+    if (p->flow_model != LBPC_FLOW_NONE) {
+        d.s_nu = 1.0 / (3.0 * d.nu + 0.5);  // Eq. 59
+        d.tau_f = 1.0 / d.s_nu;
+        if (p->flow_model == LBPC_FLOW_SRT) {
+            d.s_e = d.s_eps = d.s_q = d.s_pi = d.s_t = d.s_nu;
+        } else {
+            d.s_e = p->s_e > 0 ? p->s_e : 1.19;
+            d.s_eps = p->s_eps > 0 ? p->s_eps : 1.4;
+            d.s_q = p->s_q > 0 ? p->s_q : 1.2;
+            d.s_pi = p->s_pi > 0 ? p->s_pi : 1.4;
+            d.s_t = p->s_t > 0 ? p->s_t : 1.98;
+        }
+        const double r[6] = {d.s_nu, d.s_e, d.s_eps, d.s_q, d.s_pi, d.s_t};
+        for (double v : r)
+            if (!(v > 0 && v < 2)) { e = "flow relaxation rate outside (0, 2)"; return false; }
+    }
+    if (!(d.sigma_chi > 0 && d.sigma_chi < 2) || !(d.sigma4 > 0 && d.sigma4 < 2)) {
+        e = "enthalpy relaxation rate outside (0, 2)"; return false;
+    }
+    return true;
+}
+
+template <class C>
+inline void fill_coef(Coef<C>& c, const lbpc_params& p, const Derived& d) {
+    c.Tm = (C)p.Tm;
+    c.Cps = (C)p.Cp_s;
+    c.Cpl = (C)p.Cp_l;
+    c.Cps_inv = (C)(1.0 / p.Cp_s);
+    c.Cpl_inv = (C)(1.0 / p.Cp_l);
+    c.L = (C)d.L;
+    c.L_inv = (C)(1.0 / d.L);
+    c.Tref = (C)p.Tref;
+    c.gbeta = (C)d.gbeta;
+    c.wa_cref = (C)(0.5 * p.omega_T * p.Cp_ref);
+    c.wT_cref = (C)(p.omega_T * p.Cp_ref);
+    c.sig_chi = (C)d.sigma_chi;
+    c.sig4 = c.sig5 = c.sig6 = (C)d.sigma4;
+    c.s_e = (C)d.s_e;
+    c.s_eps = (C)d.s_eps;
+    c.s_q = (C)d.s_q;
+    c.s_nu = (C)d.s_nu;
+    c.s_pi = (C)d.s_pi;
+    c.s_t = (C)d.s_t;
+    const bool shifted = p.precision == LBPC_FP16S || p.precision == LBPC_BF16S;
+    c.fshift0 = (C)(shifted ? 1.0 / 3.0 : 0.0);
+    c.fshift1 = (C)(shifted ? 1.0 / 18.0 : 0.0);
+    c.fshift2 = (C)(shifted ? 1.0 / 36.0 : 0.0);
+    c.gshift = (C)(shifted ? 0.5 * p.omega_T * p.Cp_ref * p.Tref : 0.0);
+}
+
+// Kernel argument block of a validated parameter block; Tw[f] are the device (or host,
+// for host-side evaluation) wall temperature fields of the six faces.
+inline void fill_args(Args& a, int nx, int ny, int nz, const lbpc_params& p, const Derived& d,
+                      double* const Tw[6]) {
+    std::memset(&a, 0, sizeof a);
+    a.nx = nx; a.ny = ny; a.nz = nz; a.N = nx * ny * nz;
+    for (int ax = 0; ax < 3; ax++) a.per[ax] = p.bc[2 * ax] == LBPC_PERIODIC;
+    for (int f = 0; f < 6; f++) {
+        a.wall[f] = p.bc[f] != LBPC_PERIODIC;
+        a.wall_iso[f] = p.bc[f] == LBPC_ISOTHERMAL;
+        a.Tw[f] = Tw[f];
+    }
+    a.flow = p.flow_model != LBPC_FLOW_NONE;
+    a.hs = d.hs;
+    a.L = d.L;
+    fill_coef(a.cf, p, d);
+    fill_coef(a.cd, p, d);
+}
+
+}  // namespace lbpc

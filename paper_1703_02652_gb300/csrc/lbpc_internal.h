@@ -1,0 +1,80 @@
+// lbpc_internal.h -- structures shared by the host side of the C ABI and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lbpc.h"
+
+namespace lbpc {
+
+// Per-run constants in one compute precision C (float for the 32/16-bit storage modes,
+// double for FP64 storage), so kernels never convert constants at run time.
+template <class C>
+struct Coef {
+    C Tm, Cps, Cpl, Cps_inv, Cpl_inv, L, L_inv, Tref, gbeta;
+    C wa_cref;  // (omega_T / 2) Cp_ref: weight times Cp_ref of the six moving g populations
+    C wT_cref;  // omega_T Cp_ref: anti-bounce-back source per unit wall temperature
+    C sig_chi, sig4, sig5, sig6;           // D3Q7 rates (Eq. 23, 47)
+    C s_e, s_eps, s_q, s_nu, s_pi, s_t;    // D3Q19 rates (Eq. 52)
+    C fshift0, fshift1, fshift2;           // storage shifts of f: rest / axis / diagonal weight
+    C gshift;                              // storage shift of g_1..6
+};
+
+struct Args {
+    int nx, ny, nz, N;   // N = nx*ny*nz < 2^31
+    int per[3];          // periodic axes
+    int wall_iso[6];     // face is an isothermal wall (anti-bounce-back of g)
+    int wall[6];         // face is a wall (not periodic)
+    const double* Tw[6]; // per-face wall temperature fields (device)
+    int flow;            // flow lattice present
+    double hs, L;        // FP64 copies for the enthalpy inversion
+    Coef<float> cf;
+    Coef<double> cd;
+};
+
+// How populations are laid out in memory for a gather.
+enum Layout : int {
+    LAYOUT_PULL = 0,      // two-lattice pull: slot a at node x holds f*_a(x) of the last step
+    LAYOUT_AA_NATURAL = 1,// AA after an even number of steps: slot a at x holds f_a(x)
+    LAYOUT_AA_SWAPPED = 2 // AA after an odd number of steps: slot abar at x holds f*_a(x)
+};
+
+// Step kernel flavours.
+enum StepKind : int { STEP_PULL = 0, STEP_AA_EVEN = 1, STEP_AA_ODD = 2 };
+
+struct MacroOut {
+    double *T, *fl, *h, *rho, *ux, *uy, *uz;  // any may be null
+    double* partial;   // [RED_BLOCKS][NRED] block partial sums (null: no reductions)
+    double* lines;     // [3][nx] f_l on the three front lines (null: skip)
+};
+
+constexpr int NRED = 6;  // sum f_l, sum h, sum rho, wall flux -x, FD gradient -x, nan count
+constexpr int RED_BLOCKS = 1216;  // 8 x 152 SMs
+constexpr int RED_THREADS = 256;
+
+struct Launchers {
+    void (*step)(const Args&, StepKind, const void* fs, void* fd, const void* gs, void* gd,
+                 double* hp, cudaStream_t);
+    void (*macro)(const Args&, Layout, const void* f, const void* g, const double* hp,
+                  const MacroOut&, cudaStream_t);
+    // write populations from a pre-collision state Q (f: 19N FP64 or null = rest
+    // equilibrium; g: 7N FP64 or null = equilibrium of h0) into `layout`, then h'.
+    void (*init)(const Args&, Layout, const double* Qf, const double* Qg, const double* h0,
+                 void* f, void* g, double* hp, cudaStream_t);
+    // pre-collision populations in FP64 (f: 19N or null, g: 7N)
+    void (*dist)(const Args&, Layout, const void* f, const void* g, const double* hp,
+                 double* Qf, double* Qg, cudaStream_t);
+    size_t store_bytes;  // bytes of one stored population value
+};
+
+const Launchers& launchers_f64();
+const Launchers& launchers_f32();
+const Launchers& launchers_f16();
+const Launchers& launchers_bf16();
+
+void finalize_reduction(const Args& a, const double* partial, const double* lines,
+                        const double* face_area_inv, double nu_scale, double fd_scale,
+                        double step, double* result, double* hist_row, int hist_write,
+                        cudaStream_t s);
+
+}  // namespace lbpc

@@ -1,0 +1,798 @@
+// lbpc_kernels.cuh -- device code of the coupled flow + enthalpy lattice Boltzmann step.
+//
+// Included once per storage precision by lbpc_kern_{f64,f32,f16,bf16}.cu, which define
+// LBPC_PREC and the name of the launcher table.  Everything here is written for the
+// structure of the two lattices (Eq. 3, Eq. 48) rather than with dense matrices: the
+// D3Q19 moment transform (Eq. 51) is evaluated as grouped sums over the axis pairs and
+// the three diagonal planes, and the D3Q7 MRT collision (Eq. 21-25) acts directly on
+// the deviations g_a - g_a^eq of the six moving populations.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "lbpc_internal.h"
+
+#define LBPC_HD __host__ __device__ __forceinline__
+
+namespace lbpc {
+
+// ---------------------------------------------------------------------------------
+// Storage codecs.  16-bit modes store the deviation from a fixed shift (the rest
+// weight of f, (omega_T / 2) Cp_ref T_ref for g) and compute in FP32.
+// ---------------------------------------------------------------------------------
+template <int P> struct Store;
+template <> struct Store<LBPC_FP64> {
+    using T = double; using C = double;
+    static LBPC_HD C dec(T v, C) { return v; }
+    static LBPC_HD T enc(C v, C) { return v; }
+};
+template <> struct Store<LBPC_FP32> {
+    using T = float; using C = float;
+    static LBPC_HD C dec(T v, C) { return v; }
+    static LBPC_HD T enc(C v, C) { return v; }
+};
+template <> struct Store<LBPC_FP16S> {
+    using T = __half; using C = float;
+    static LBPC_HD C dec(T v, C s) { return __half2float(v) + s; }
+    static LBPC_HD T enc(C v, C s) { return __float2half_rn(v - s); }
+};
+template <> struct Store<LBPC_BF16S> {
+    using T = __nv_bfloat16; using C = float;
+    static LBPC_HD C dec(T v, C s) { return __bfloat162float(v) + s; }
+    static LBPC_HD T enc(C v, C s) { return __float2bfloat16_rn(v - s); }
+};
+
+template <class C> LBPC_HD const Coef<C>& coef(const Args& a);
+template <> LBPC_HD const Coef<float>& coef<float>(const Args& a) { return a.cf; }
+template <> LBPC_HD const Coef<double>& coef<double>(const Args& a) { return a.cd; }
+
+// D3Q19 velocities in the order of Eq. 48: X(index, ex, ey, ez, opposite).
+#define LBPC_Q19(X)                                                                     \
+    X(0, 0, 0, 0, 0) X(1, 1, 0, 0, 2) X(2, -1, 0, 0, 1) X(3, 0, 1, 0, 4)                \
+    X(4, 0, -1, 0, 3) X(5, 0, 0, 1, 6) X(6, 0, 0, -1, 5) X(7, 1, 1, 0, 10)              \
+    X(8, -1, 1, 0, 9) X(9, 1, -1, 0, 8) X(10, -1, -1, 0, 7) X(11, 1, 0, 1, 14)          \
+    X(12, -1, 0, 1, 13) X(13, 1, 0, -1, 12) X(14, -1, 0, -1, 11) X(15, 0, 1, 1, 18)     \
+    X(16, 0, -1, 1, 17) X(17, 0, 1, -1, 16) X(18, 0, -1, -1, 15)
+// D3Q7 moving velocities in the order of Eq. 3: X(index, ex, ey, ez, opposite).
+#define LBPC_Q7(X)                                                                      \
+    X(1, 1, 0, 0, 2) X(2, -1, 0, 0, 1) X(3, 0, 1, 0, 4) X(4, 0, -1, 0, 3)               \
+    X(5, 0, 0, 1, 6) X(6, 0, 0, -1, 5)
+
+// Offsets (in nodes) to the neighbours at x-1 / x+1 etc. with periodic wrap, and
+// whether that neighbour lies behind a wall.
+struct Nb {
+    int oxm, oxp, oym, oyp, ozm, ozp;
+    bool wxm, wxp, wym, wyp, wzm, wzp;
+};
+
+LBPC_HD Nb make_nb(const Args& a, int x, int y, int z) {
+    Nb b;
+    const int sy = a.nx, sz = a.nx * a.ny;
+    b.oxm = (x == 0) ? a.nx - 1 : -1;
+    b.oxp = (x == a.nx - 1) ? -(a.nx - 1) : 1;
+    b.oym = (y == 0) ? (a.ny - 1) * sy : -sy;
+    b.oyp = (y == a.ny - 1) ? -(a.ny - 1) * sy : sy;
+    b.ozm = (z == 0) ? (a.nz - 1) * sz : -sz;
+    b.ozp = (z == a.nz - 1) ? -(a.nz - 1) * sz : sz;
+    b.wxm = (x == 0) && a.wall[0];
+    b.wxp = (x == a.nx - 1) && a.wall[1];
+    b.wym = (y == 0) && a.wall[2];
+    b.wyp = (y == a.ny - 1) && a.wall[3];
+    b.wzm = (z == 0) && a.wall[4];
+    b.wzp = (z == a.nz - 1) && a.wall[5];
+    return b;
+}
+
+// Upwind neighbour x - e of velocity e = (EX, EY, EZ): offset and wall test.
+template <int EX, int EY, int EZ>
+LBPC_HD int up_off(const Nb& b) {
+    return (EX == 1 ? b.oxm : EX == -1 ? b.oxp : 0) + (EY == 1 ? b.oym : EY == -1 ? b.oyp : 0) +
+           (EZ == 1 ? b.ozm : EZ == -1 ? b.ozp : 0);
+}
+template <int EX, int EY, int EZ>
+LBPC_HD bool up_wall(const Nb& b) {
+    return (EX == 1 && b.wxm) || (EX == -1 && b.wxp) || (EY == 1 && b.wym) ||
+           (EY == -1 && b.wyp) || (EZ == 1 && b.wzm) || (EZ == -1 && b.wzp);
+}
+
+// Index of a node inside the temperature field of face `face`.
+LBPC_HD int face_index(const Args& a, int face, int x, int y, int z) {
+    return face < 2 ? y + a.ny * z : (face < 4 ? x + a.nx * z : x + a.nx * y);
+}
+
+template <class C>
+LBPC_HD C fshift(const Coef<C>& k, int q) {
+    return q == 0 ? k.fshift0 : (q < 7 ? k.fshift1 : k.fshift2);
+}
+
+// Anti-bounce-back source of a g population entering through face `face` (isothermal).
+template <class C>
+LBPC_HD C abb_source(const Args& a, const Coef<C>& k, int face, int x, int y,
+                                        int z) {
+    return k.wT_cref * (C)a.Tw[face][face_index(a, face, x, y, z)];
+}
+
+// ---------------------------------------------------------------------------------
+// Gathers: pre-collision populations of node n for each memory layout.
+// ---------------------------------------------------------------------------------
+template <int P, int LAYOUT, bool NC>
+LBPC_HD typename Store<P>::T ldv(const typename Store<P>::T* p) {
+#if defined(__CUDA_ARCH__)
+    if constexpr (NC) return __ldg(p);
+#endif
+    return *p;
+}
+
+template <int P, int LAYOUT, bool NC>
+LBPC_HD void gather_f(const Args& a, const Nb& b, int n,
+                                         const typename Store<P>::T* fs,
+                                         typename Store<P>::C* f) {
+    using S = Store<P>;
+    using C = typename S::C;
+    const Coef<C>& k = coef<C>(a);
+    const size_t N = (size_t)a.N;
+#define LBPC_GF(q, ex, ey, ez, op)                                                       \
+    {                                                                                   \
+        int idx;                                                                        \
+        int slot;                                                                       \
+        if constexpr (LAYOUT == LAYOUT_AA_NATURAL) {                                    \
+            idx = n; slot = q;                                                          \
+        } else {                                                                        \
+            const bool w = up_wall<ex, ey, ez>(b);                                      \
+            idx = w ? n : n + up_off<ex, ey, ez>(b);                                    \
+            if constexpr (LAYOUT == LAYOUT_PULL) slot = w ? op : q;                      \
+            else slot = w ? q : op;                                                     \
+        }                                                                               \
+        f[q] = S::dec(ldv<P, LAYOUT, NC>(fs + (size_t)slot * N + idx), fshift(k, q));    \
+    }
+    LBPC_Q19(LBPC_GF)
+#undef LBPC_GF
+}
+
+// g_1..6 (g[0] is not gathered: the rest population is the FP64 channel h').  The g
+// lattice holds six planes: population q lives in plane q - 1.
+template <int P, int LAYOUT, bool NC>
+LBPC_HD void gather_g(const Args& a, const Nb& b, int n, int x, int y, int z,
+                                         const typename Store<P>::T* gs,
+                                         typename Store<P>::C* g) {
+    using S = Store<P>;
+    using C = typename S::C;
+    const Coef<C>& k = coef<C>(a);
+    const size_t N = (size_t)a.N;
+#define LBPC_GG(q, ex, ey, ez, op)                                                       \
+    {                                                                                   \
+        if constexpr (LAYOUT == LAYOUT_AA_NATURAL) {                                    \
+            g[q] = S::dec(ldv<P, LAYOUT, NC>(gs + (size_t)(q - 1) * N + n), k.gshift);         \
+        } else {                                                                        \
+            const bool w = up_wall<ex, ey, ez>(b);                                      \
+            const int idx = w ? n : n + up_off<ex, ey, ez>(b);                          \
+            int slot;                                                                   \
+            if constexpr (LAYOUT == LAYOUT_PULL) slot = w ? op : q;                      \
+            else slot = w ? q : op;                                                     \
+            C v = S::dec(ldv<P, LAYOUT, NC>(gs + (size_t)(slot - 1) * N + idx), k.gshift);     \
+            if (w && a.wall_iso[q - 1]) v = -v + abb_source(a, k, q - 1, x, y, z);       \
+            g[q] = v;                                                                   \
+        }                                                                               \
+    }
+    LBPC_Q7(LBPC_GG)
+#undef LBPC_GG
+}
+
+// ---------------------------------------------------------------------------------
+// Scatters of post-collision populations.
+// ---------------------------------------------------------------------------------
+template <int P, int KIND>
+LBPC_HD void scatter_f(const Args& a, const Nb& b, int n,
+                                          typename Store<P>::T* fd,
+                                          const typename Store<P>::C* f) {
+    using S = Store<P>;
+    using C = typename S::C;
+    const Coef<C>& k = coef<C>(a);
+    const size_t N = (size_t)a.N;
+#define LBPC_SF(q, ex, ey, ez, op)                                                       \
+    {                                                                                   \
+        const auto v = S::enc(f[q], fshift(k, q));                                      \
+        if constexpr (KIND == STEP_PULL) {                                              \
+            fd[(size_t)q * N + n] = v;                                                  \
+        } else if constexpr (KIND == STEP_AA_EVEN) {                                    \
+            fd[(size_t)op * N + n] = v;                                                 \
+        } else { /* downwind neighbour x + e is the upwind neighbour of -e */           \
+            const bool w = up_wall<-(ex), -(ey), -(ez)>(b);                             \
+            if (w) fd[(size_t)op * N + n] = v;                                          \
+            else fd[(size_t)q * N + n + up_off<-(ex), -(ey), -(ez)>(b)] = v;            \
+        }                                                                               \
+    }
+    LBPC_Q19(LBPC_SF)
+#undef LBPC_SF
+}
+
+// Returns sum over a of the stored (rounded) g*_a, in FP64.
+template <int P, int KIND>
+LBPC_HD double scatter_g(const Args& a, const Nb& b, int n, int x, int y,
+                                            int z, typename Store<P>::T* gd,
+                                            const typename Store<P>::C* g) {
+    using S = Store<P>;
+    using C = typename S::C;
+    const Coef<C>& k = coef<C>(a);
+    const size_t N = (size_t)a.N;
+    double sum = 0.0;
+#define LBPC_SG(q, ex, ey, ez, op)                                                       \
+    {                                                                                   \
+        const auto v = S::enc(g[q], k.gshift);                                          \
+        sum += (double)S::dec(v, k.gshift);                                             \
+        if constexpr (KIND == STEP_PULL) {                                              \
+            gd[(size_t)(q - 1) * N + n] = v;                                                  \
+        } else if constexpr (KIND == STEP_AA_EVEN) {                                    \
+            gd[(size_t)(op - 1) * N + n] = v;                                                 \
+        } else {                                                                        \
+            const bool w = up_wall<-(ex), -(ey), -(ez)>(b);                             \
+            if (w) {                                                                    \
+                auto vb = v;                                                            \
+                if (a.wall_iso[op - 1])                                                 \
+                    vb = S::enc(-S::dec(v, k.gshift) + abb_source(a, k, op - 1, x, y, z), \
+                                k.gshift);                                              \
+                gd[(size_t)(op - 1) * N + n] = vb;                                            \
+            } else {                                                                    \
+                gd[(size_t)(q - 1) * N + n + up_off<-(ex), -(ey), -(ez)>(b)] = v;             \
+            }                                                                           \
+        }                                                                               \
+    }
+    LBPC_Q7(LBPC_SG)
+#undef LBPC_SG
+    return sum;
+}
+
+// ---------------------------------------------------------------------------------
+// Local physics.
+// ---------------------------------------------------------------------------------
+
+// Eq. 2 inverted (h = C_p T + f_l L; solid for h <= h_s, liquid for h >= h_s + L, mushy
+// at T_m in between).  The cancelling subtraction h - h_s is done in FP64.
+template <class C>
+LBPC_HD void invert_h(const Args& a, const Coef<C>& k, double h, C& T, C& fl) {
+    const C d = (C)(h - a.hs);
+    if (d <= C(0)) {
+        fl = C(0);
+        T = k.Tm + d * k.Cps_inv;
+    } else if (d >= k.L) {
+        fl = C(1);
+        T = k.Tm + (d - k.L) * k.Cpl_inv;
+    } else {
+        fl = d * k.L_inv;
+        T = k.Tm;
+    }
+}
+
+// Density, momentum, Boussinesq force (Eq. 55), solid-phase force -2 (1 - f_l) u* and the
+// velocity of Eq. 56 (rho_0 = 1): u = f_l (j + F_b / 2).
+template <class C>
+LBPC_HD void flow_macro(const C* f, const Coef<C>& k, C T, C fl, C& rho, C& jx,
+                                           C& jy, C& jz, C& ux, C& uy, C& uz, C& Fx, C& Fy,
+                                           C& Fz) {
+    rho = ((f[0] + (f[1] + f[2])) + ((f[3] + f[4]) + (f[5] + f[6]))) +
+          (((f[7] + f[8]) + (f[9] + f[10])) + ((f[11] + f[12]) + (f[13] + f[14])) +
+           ((f[15] + f[16]) + (f[17] + f[18])));
+    jx = (f[1] - f[2]) + (f[7] - f[8] + f[9] - f[10]) + (f[11] - f[12] + f[13] - f[14]);
+    jy = (f[3] - f[4]) + (f[7] + f[8] - f[9] - f[10]) + (f[15] - f[16] + f[17] - f[18]);
+    jz = (f[5] - f[6]) + (f[11] + f[12] - f[13] - f[14]) + (f[15] + f[16] - f[17] - f[18]);
+    const C Fb = k.gbeta * (T - k.Tref);
+    const C usx = jx, usy = jy, usz = jz + C(0.5) * Fb;
+    const C damp = C(-2) * (C(1) - fl);
+    Fx = damp * usx;
+    Fy = damp * usy;
+    Fz = Fb + damp * usz;
+    ux = fl * usx;
+    uy = fl * usy;
+    uz = fl * usz;
+}
+
+// D3Q19 MRT collision with forcing (Eq. 49-54) in correction form:
+// f* = f + M^-1 [ -Lambda (m - m^eq) + (I - Lambda/2) FF ], with M^-1 = M^T diag(1/|row|^2).
+template <class C>
+LBPC_HD void collide_flow(C* f, const Coef<C>& k, C T, C fl, C& ux, C& uy,
+                                             C& uz) {
+    // grouped sums: axis pairs and the xy, xz, yz diagonal quadruples
+    const C a1 = f[1] + f[2], b1 = f[1] - f[2];
+    const C a3 = f[3] + f[4], b3 = f[3] - f[4];
+    const C a5 = f[5] + f[6], b5 = f[5] - f[6];
+    const C sxy = (f[7] + f[8]) + (f[9] + f[10]);
+    const C xy_x = (f[7] - f[8]) + (f[9] - f[10]);
+    const C xy_y = (f[7] + f[8]) - (f[9] + f[10]);
+    const C xy_p = (f[7] - f[8]) - (f[9] - f[10]);
+    const C sxz = (f[11] + f[12]) + (f[13] + f[14]);
+    const C xz_x = (f[11] - f[12]) + (f[13] - f[14]);
+    const C xz_z = (f[11] + f[12]) - (f[13] + f[14]);
+    const C xz_p = (f[11] - f[12]) - (f[13] - f[14]);
+    const C syz = (f[15] + f[16]) + (f[17] + f[18]);
+    const C yz_y = (f[15] - f[16]) + (f[17] - f[18]);
+    const C yz_z = (f[15] + f[16]) - (f[17] + f[18]);
+    const C yz_p = (f[15] - f[16]) - (f[17] - f[18]);
+    const C sax = a1 + a3 + a5, sdg = sxy + sxz + syz;
+
+    const C rho = f[0] + sax + sdg;
+    const C jx = b1 + xy_x + xz_x, jy = b3 + xy_y + yz_y, jz = b5 + xz_z + yz_z;
+    // non-conserved moments (rows 1, 2, 4, 6, 8-18 of Eq. 51)
+    const C m1 = C(-30) * f[0] - C(11) * sax + C(8) * sdg;
+    const C m2 = C(12) * f[0] - C(4) * sax + sdg;
+    const C m4 = C(-4) * b1 + xy_x + xz_x;
+    const C m6 = C(-4) * b3 + xy_y + yz_y;
+    const C m8 = C(-4) * b5 + xz_z + yz_z;
+    const C m9 = C(2) * a1 - a3 - a5 + sxy + sxz - C(2) * syz;
+    const C m10 = C(-4) * a1 + C(2) * (a3 + a5) + sxy + sxz - C(2) * syz;
+    const C m11 = a3 - a5 + sxy - sxz;
+    const C m12 = C(2) * (a5 - a3) + sxy - sxz;
+    const C m13 = xy_p, m14 = yz_p, m15 = xz_p;
+    const C m16 = xy_x - xz_x, m17 = yz_y - xy_y, m18 = xz_z - yz_z;
+
+    // forces and velocity (Eq. 55-56 with the solid-phase force)
+    const C Fb = k.gbeta * (T - k.Tref);
+    const C usx = jx, usy = jy, usz = jz + C(0.5) * Fb;
+    const C damp = C(-2) * (C(1) - fl);
+    const C Fx = damp * usx, Fy = damp * usy, Fz = Fb + damp * usz;
+    ux = fl * usx;
+    uy = fl * usy;
+    uz = fl * usz;
+
+    // equilibrium moments (Eq. 53) and forcing moments (Eq. 54), c = 1
+    const C uxx = ux * ux, uyy = uy * uy, uzz = uz * uz, u2 = uxx + uyy + uzz;
+    const C Fu = Fx * ux + Fy * uy + Fz * uz;
+    const C pxx_eq = rho * (C(3) * uxx - u2), pww_eq = rho * (uyy - uzz);
+    const C FFxx = C(6) * Fx * ux - C(2) * Fu, FFww = C(2) * (Fy * uy - Fz * uz);
+    const C c23 = C(2) / C(3);
+
+    // d_k = [-s_k (m_k - meq_k) + (1 - s_k/2) FF_k] / |row k|^2
+    const C he = C(1) - C(0.5) * k.s_e, hps = C(1) - C(0.5) * k.s_eps, hq = C(1) - C(0.5) * k.s_q;
+    const C hn = C(1) - C(0.5) * k.s_nu, hpi = C(1) - C(0.5) * k.s_pi;
+    const C d1 = (-k.s_e * (m1 - rho * (C(-11) + C(19) * u2)) + he * (C(38) * Fu)) * C(1.0 / 2394.0);
+    const C d2 = (-k.s_eps * (m2 - rho * (C(3) - C(5.5) * u2)) + hps * (C(-11) * Fu)) * C(1.0 / 252.0);
+    const C d3 = Fx * C(0.1), d5 = Fy * C(0.1), d7 = Fz * C(0.1);
+    const C d4 = (-k.s_q * (m4 + c23 * rho * ux) - hq * c23 * Fx) * C(1.0 / 40.0);
+    const C d6 = (-k.s_q * (m6 + c23 * rho * uy) - hq * c23 * Fy) * C(1.0 / 40.0);
+    const C d8 = (-k.s_q * (m8 + c23 * rho * uz) - hq * c23 * Fz) * C(1.0 / 40.0);
+    const C d9 = (-k.s_nu * (m9 - pxx_eq) + hn * FFxx) * C(1.0 / 36.0);
+    const C d10 = (-k.s_pi * (m10 + C(0.5) * pxx_eq) - hpi * C(0.5) * FFxx) * C(1.0 / 72.0);
+    const C d11 = (-k.s_nu * (m11 - pww_eq) + hn * FFww) * C(1.0 / 12.0);
+    const C d12 = (-k.s_pi * (m12 + C(0.5) * pww_eq) - hpi * C(0.5) * FFww) * C(1.0 / 24.0);
+    const C d13 = (-k.s_nu * (m13 - rho * ux * uy) + hn * (Fx * uy + Fy * ux)) * C(0.25);
+    const C d14 = (-k.s_nu * (m14 - rho * uy * uz) + hn * (Fy * uz + Fz * uy)) * C(0.25);
+    const C d15 = (-k.s_nu * (m15 - rho * ux * uz) + hn * (Fx * uz + Fz * ux)) * C(0.25);
+    const C d16 = -k.s_t * m16 * C(0.125);
+    const C d17 = -k.s_t * m17 * C(0.125);
+    const C d18 = -k.s_t * m18 * C(0.125);
+
+    // back-transform: f*_a = f_a + sum_k M_ka d_k (columns of Eq. 51)
+    f[0] += C(-30) * d1 + C(12) * d2;
+    const C eax = C(-11) * d1 - C(4) * d2;
+    const C ox = d3 - C(4) * d4, oy = d5 - C(4) * d6, oz = d7 - C(4) * d8;
+    const C ex1 = eax + C(2) * d9 - C(4) * d10;
+    const C ey1 = eax - d9 + C(2) * d10 + d11 - C(2) * d12;
+    const C ez1 = eax - d9 + C(2) * d10 - d11 + C(2) * d12;
+    f[1] += ex1 + ox;
+    f[2] += ex1 - ox;
+    f[3] += ey1 + oy;
+    f[4] += ey1 - oy;
+    f[5] += ez1 + oz;
+    f[6] += ez1 - oz;
+    const C edg = C(8) * d1 + d2;
+    const C X = d3 + d4, Y = d5 + d6, Z = d7 + d8;
+    const C exy = edg + d9 + d10 + d11 + d12;
+    f[7] += exy + X + Y + d13 + d16 - d17;
+    f[8] += exy - X + Y - d13 - d16 - d17;
+    f[9] += exy + X - Y - d13 + d16 + d17;
+    f[10] += exy - X - Y + d13 - d16 + d17;
+    const C exz = edg + d9 + d10 - d11 - d12;
+    f[11] += exz + X + Z + d15 - d16 + d18;
+    f[12] += exz - X + Z - d15 + d16 + d18;
+    f[13] += exz + X - Z - d15 - d16 - d18;
+    f[14] += exz - X - Z + d15 + d16 - d18;
+    const C eyz = edg - C(2) * d9 - C(2) * d10;
+    f[15] += eyz + Y + Z + d14 + d17 - d18;
+    f[16] += eyz - Y + Z - d14 - d17 - d18;
+    f[17] += eyz + Y - Z - d14 + d17 + d18;
+    f[18] += eyz - Y - Z + d14 - d17 + d18;
+}
+
+// D3Q7 enthalpy collision on the six moving populations (Eq. 21-25; SRT when every
+// rate equals 1/tau_g).  With d_a = g_a - g_a^eq, d_0 = -sum d_a (h is conserved), the
+// moments of d are m1..m3 (odd pairs), m4 = -7 S, m5, m6; g* = g^eq + d - N^-1 R N d.
+template <class C>
+LBPC_HD void collide_enth(C* g, const Coef<C>& k, C T, C fl, C ux, C uy,
+                                             C uz) {
+    const C Cp = fl * k.Cpl + (C(1) - fl) * k.Cps;
+    const C cT = k.wa_cref * T;       // even part of g^eq_a (Eq. 7)
+    const C vT = C(0.5) * Cp * T;     // (omega_a / c_sT^2) Cp T = Cp T / 2
+    const C e1 = cT + vT * ux, e2 = cT - vT * ux;
+    const C e3 = cT + vT * uy, e4 = cT - vT * uy;
+    const C e5 = cT + vT * uz, e6 = cT - vT * uz;
+    const C d1 = g[1] - e1, d2 = g[2] - e2, d3 = g[3] - e3, d4 = g[4] - e4, d5 = g[5] - e5,
+            d6 = g[6] - e6;
+    const C m1 = d1 - d2, m2 = d3 - d4, m3 = d5 - d6;
+    const C p12 = d1 + d2, p34 = d3 + d4, p56 = d5 + d6;
+    const C S = p12 + p34 + p56;
+    const C m5 = C(2) * p12 - (p34 + p56);
+    const C m6 = p34 - p56;
+    const C A = k.sig4 * S * C(1.0 / 6.0);
+    const C B = k.sig5 * m5;
+    const C D = k.sig6 * m6 * C(0.25);
+    const C hc = C(0.5) * k.sig_chi;
+    const C c12 = A + B * C(1.0 / 6.0);
+    const C c36 = A - B * C(1.0 / 12.0);
+    g[1] = e1 + d1 - (hc * m1 + c12);
+    g[2] = e2 + d2 - (-hc * m1 + c12);
+    g[3] = e3 + d3 - (hc * m2 + c36 + D);
+    g[4] = e4 + d4 - (-hc * m2 + c36 + D);
+    g[5] = e5 + d5 - (hc * m3 + c36 - D);
+    g[6] = e6 + d6 - (-hc * m3 + c36 - D);
+}
+
+template <class C>
+LBPC_HD double hsum6(double hprime, const C* g) {
+    double h = hprime;
+    h += (double)g[1];
+    h += (double)g[2];
+    h += (double)g[3];
+    h += (double)g[4];
+    h += (double)g[5];
+    h += (double)g[6];
+    return h;
+}
+
+// ---------------------------------------------------------------------------------
+// Node-level operations (host + device: the kernels below call them once per node).
+// ---------------------------------------------------------------------------------
+constexpr int STEP_THREADS = 128;
+
+template <int KIND> struct KindLayout;
+template <> struct KindLayout<STEP_PULL> { static constexpr int value = LAYOUT_PULL; };
+template <> struct KindLayout<STEP_AA_EVEN> { static constexpr int value = LAYOUT_AA_NATURAL; };
+template <> struct KindLayout<STEP_AA_ODD> { static constexpr int value = LAYOUT_AA_SWAPPED; };
+
+// One time step of node (x, y, z): gather (stream in, with wall rules), Eq. 2 inversion,
+// flow collision, enthalpy collision, scatter, FP64 rest channel update.
+template <int P, int KIND, bool FLOW>
+LBPC_HD void step_node(const Args& a, int x, int y, int z, const typename Store<P>::T* fs,
+                       typename Store<P>::T* fd, const typename Store<P>::T* gs,
+                       typename Store<P>::T* gd, double* hp) {
+    using S = Store<P>;
+    using C = typename S::C;
+    const Coef<C>& k = coef<C>(a);
+    const int n = x + a.nx * (y + a.ny * z);
+    const Nb b = make_nb(a, x, y, z);
+    constexpr int LAYOUT = KindLayout<KIND>::value;
+    constexpr bool NC = KIND == STEP_PULL;  // read-only path only when src != dst
+
+    C f[19], g[7];
+    if constexpr (FLOW) gather_f<P, LAYOUT, NC>(a, b, n, fs, f);
+    gather_g<P, LAYOUT, NC>(a, b, n, x, y, z, gs, g);
+    const double h = hsum6(hp[n], g);
+
+    C T, fl;
+    invert_h(a, k, h, T, fl);
+    C ux = C(0), uy = C(0), uz = C(0);
+    if constexpr (FLOW) {
+        collide_flow(f, k, T, fl, ux, uy, uz);
+        scatter_f<P, KIND>(a, b, n, fd, f);
+    }
+    collide_enth(g, k, T, fl, ux, uy, uz);
+    const double sout = scatter_g<P, KIND>(a, b, n, x, y, z, gd, g);
+    hp[n] = h - sout;
+}
+
+// Macroscopic state of node n and its contributions to the diagnostics sums
+// (acc: sum f_l, sum h, sum rho, -x wall flux, -x wall gradient, non-finite count).
+template <int P, int LAYOUT, bool FLOW>
+LBPC_HD void macro_node(const Args& a, int n, const typename Store<P>::T* fs,
+                        const typename Store<P>::T* gs, const double* hp, const MacroOut& out,
+                        double* acc) {
+    using S = Store<P>;
+    using C = typename S::C;
+    const Coef<C>& k = coef<C>(a);
+    const int x = n % a.nx, y = (n / a.nx) % a.ny, z = n / (a.nx * a.ny);
+    const Nb b = make_nb(a, x, y, z);
+    C f[19], g[7];
+    if constexpr (FLOW) gather_f<P, LAYOUT, true>(a, b, n, fs, f);
+    gather_g<P, LAYOUT, true>(a, b, n, x, y, z, gs, g);
+    const double h = hsum6(hp[n], g);
+    C T, fl;
+    invert_h(a, k, h, T, fl);
+    C rho = C(0), ux = C(0), uy = C(0), uz = C(0);
+    if constexpr (FLOW) {
+        C jx, jy, jz, Fx, Fy, Fz;
+        flow_macro(f, k, T, fl, rho, jx, jy, jz, ux, uy, uz, Fx, Fy, Fz);
+    }
+    if (out.T) out.T[n] = (double)T;
+    if (out.fl) out.fl[n] = (double)fl;
+    if (out.h) out.h[n] = h;
+    if (out.rho) out.rho[n] = (double)rho;
+    if (out.ux) out.ux[n] = (double)ux;
+    if (out.uy) out.uy[n] = (double)uy;
+    if (out.uz) out.uz[n] = (double)uz;
+    if (acc) {
+        acc[0] += (double)fl;
+        acc[1] += h;
+        acc[2] += (double)rho;
+        if (x == 0) {
+            const double Tw = a.Tw[0][y + a.ny * z];
+            if (a.wall_iso[0]) acc[3] += 2.0 * (double)g[1] - (double)k.wT_cref * Tw;
+            acc[4] += (Tw - (double)T) * 2.0;
+        }
+        if (!isfinite(h) || !isfinite((double)rho)) acc[5] += 1.0;
+    }
+    if (out.lines && y == a.ny / 2) {
+        if (z == a.nz / 4) out.lines[x] = (double)fl;
+        if (z == a.nz / 2) out.lines[a.nx + x] = (double)fl;
+        if (z == (3 * a.nz) / 4) out.lines[2 * a.nx + x] = (double)fl;
+    }
+}
+
+// Value of pre-collision population q of node m in the state to load: Q when given,
+// else the rest equilibrium of f (rho = 1, u = 0) and g^eq(h0, T(h0), 0) of Eq. 7.
+template <class C>
+LBPC_HD double state_f(const double* Qf, size_t N, int q, int m) {
+    return Qf ? Qf[(size_t)q * N + m] : (q == 0 ? 1.0 / 3.0 : (q < 7 ? 1.0 / 18.0 : 1.0 / 36.0));
+}
+template <class C>
+LBPC_HD double state_g(const Args& a, const Coef<C>& k, const double* Qg, const double* h0,
+                       int q, int m) {
+    if (Qg) return Qg[(size_t)q * a.N + m];
+    C T, fl;
+    invert_h(a, k, h0[m], T, fl);
+    return (double)(k.wa_cref * T);
+}
+
+// Write the slots of node (x, y, z) so that a gather in LAYOUT returns the state Q.
+// For the pull layout a slot holds the value its downwind neighbour pulls; slots whose
+// downwind neighbour lies behind a wall feed the node's own bounce-back.
+template <int P, int LAYOUT, bool FLOW>
+LBPC_HD void init_node(const Args& a, int x, int y, int z, const double* Qf, const double* Qg,
+                       const double* h0, typename Store<P>::T* fd, typename Store<P>::T* gd) {
+    using S = Store<P>;
+    using C = typename S::C;
+    const Coef<C>& k = coef<C>(a);
+    const int n = x + a.nx * (y + a.ny * z);
+    const Nb b = make_nb(a, x, y, z);
+    const size_t N = (size_t)a.N;
+    if constexpr (FLOW) {
+#define LBPC_IF(q, ex, ey, ez, op)                                                       \
+        {                                                                               \
+            double v;                                                                   \
+            if constexpr (LAYOUT == LAYOUT_AA_NATURAL) v = state_f<C>(Qf, N, q, n);     \
+            else {                                                                      \
+                const bool w = up_wall<-(ex), -(ey), -(ez)>(b);                         \
+                v = w ? state_f<C>(Qf, N, op, n)                                        \
+                      : state_f<C>(Qf, N, q, n + up_off<-(ex), -(ey), -(ez)>(b));       \
+            }                                                                           \
+            fd[(size_t)q * N + n] = S::enc((C)v, fshift(k, q));                         \
+        }
+        LBPC_Q19(LBPC_IF)
+#undef LBPC_IF
+    }
+#define LBPC_IG(q, ex, ey, ez, op)                                                       \
+    {                                                                                   \
+        double v;                                                                       \
+        if constexpr (LAYOUT == LAYOUT_AA_NATURAL) v = state_g(a, k, Qg, h0, q, n);     \
+        else {                                                                          \
+            const bool w = up_wall<-(ex), -(ey), -(ez)>(b);                             \
+            if (w) {                                                                    \
+                v = state_g(a, k, Qg, h0, op, n);                                       \
+                if (a.wall_iso[op - 1])                                                 \
+                    v = (double)k.wT_cref * a.Tw[op - 1][face_index(a, op - 1, x, y, z)] - v; \
+            } else {                                                                    \
+                v = state_g(a, k, Qg, h0, q, n + up_off<-(ex), -(ey), -(ez)>(b));       \
+            }                                                                           \
+        }                                                                               \
+        gd[(size_t)(q - 1) * N + n] = S::enc((C)v, k.gshift);                                 \
+    }
+    LBPC_Q7(LBPC_IG)
+#undef LBPC_IG
+}
+
+// h' = h - sum_a g_a(gathered), so that the stored state reproduces h.
+template <int P, int LAYOUT>
+LBPC_HD void init_hprime_node(const Args& a, int x, int y, int z, const double* Qg,
+                              const double* h0, const typename Store<P>::T* gs, double* hp) {
+    using C = typename Store<P>::C;
+    const int n = x + a.nx * (y + a.ny * z);
+    const Nb b = make_nb(a, x, y, z);
+    double h;
+    if (Qg) {
+        h = 0.0;
+        for (int q = 0; q < 7; q++) h += Qg[(size_t)q * a.N + n];
+    } else {
+        h = h0[n];
+    }
+    C g[7];
+    gather_g<P, LAYOUT, true>(a, b, n, x, y, z, gs, g);
+    double s = 0.0;
+    for (int q = 1; q < 7; q++) s += (double)g[q];
+    hp[n] = h - s;
+}
+
+// Pre-collision populations of node (x, y, z) in FP64 (g_0 = h').
+template <int P, int LAYOUT, bool FLOW>
+LBPC_HD void dist_node(const Args& a, int x, int y, int z, const typename Store<P>::T* fs,
+                       const typename Store<P>::T* gs, const double* hp, double* Qf, double* Qg) {
+    using C = typename Store<P>::C;
+    const int n = x + a.nx * (y + a.ny * z);
+    const Nb b = make_nb(a, x, y, z);
+    const size_t N = (size_t)a.N;
+    C g[7];
+    gather_g<P, LAYOUT, true>(a, b, n, x, y, z, gs, g);
+    Qg[n] = hp[n];
+    for (int q = 1; q < 7; q++) Qg[(size_t)q * N + n] = (double)g[q];
+    if constexpr (FLOW) {
+        if (Qf) {
+            C f[19];
+            gather_f<P, LAYOUT, true>(a, b, n, fs, f);
+            for (int q = 0; q < 19; q++) Qf[(size_t)q * N + n] = (double)f[q];
+        }
+    }
+}
+
+#if defined(__CUDACC__)
+// ---------------------------------------------------------------------------------
+// Kernels: one thread per node on a (x-block, y-block, z) grid.
+// ---------------------------------------------------------------------------------
+#define LBPC_NODE_XYZ                                                                    \
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;                                \
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;                                \
+    const int z = blockIdx.z;                                                           \
+    if (x >= a.nx || y >= a.ny) return;
+
+template <int P, int KIND, bool FLOW>
+__global__ void __launch_bounds__(STEP_THREADS)
+k_step(const __grid_constant__ Args a, const typename Store<P>::T* fs, typename Store<P>::T* fd,
+       const typename Store<P>::T* gs, typename Store<P>::T* gd, double* __restrict__ hp) {
+    LBPC_NODE_XYZ
+    step_node<P, KIND, FLOW>(a, x, y, z, fs, fd, gs, gd, hp);
+}
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Macroscopic fields of the current state and FP64 block partial sums for diagnostics
+// (grid-stride over nodes; one partial row per block, summed later in a fixed order).
+template <int P, int LAYOUT, bool FLOW>
+__global__ void __launch_bounds__(RED_THREADS)
+k_macro(const __grid_constant__ Args a, const typename Store<P>::T* __restrict__ fs,
+        const typename Store<P>::T* __restrict__ gs, const double* __restrict__ hp,
+        const MacroOut out) {
+    double acc[NRED] = {0, 0, 0, 0, 0, 0};
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < a.N; n += gridDim.x * blockDim.x)
+        macro_node<P, LAYOUT, FLOW>(a, n, fs, gs, hp, out, out.partial ? acc : nullptr);
+    if (!out.partial) return;
+    __shared__ double sh[RED_THREADS / 32][NRED];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NRED; i++) {
+        const double v = warp_sum(acc[i]);
+        if (lane == 0) sh[wid][i] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < NRED) {
+        double s = 0.0;
+        for (int w = 0; w < RED_THREADS / 32; w++) s += sh[w][threadIdx.x];
+        out.partial[blockIdx.x * NRED + threadIdx.x] = s;
+    }
+}
+
+template <int P, int LAYOUT, bool FLOW>
+__global__ void __launch_bounds__(STEP_THREADS)
+k_init(const __grid_constant__ Args a, const double* __restrict__ Qf, const double* __restrict__ Qg,
+       const double* __restrict__ h0, typename Store<P>::T* fd, typename Store<P>::T* gd) {
+    LBPC_NODE_XYZ
+    init_node<P, LAYOUT, FLOW>(a, x, y, z, Qf, Qg, h0, fd, gd);
+}
+
+template <int P, int LAYOUT>
+__global__ void __launch_bounds__(STEP_THREADS)
+k_init_hprime(const __grid_constant__ Args a, const double* __restrict__ Qg,
+              const double* __restrict__ h0, const typename Store<P>::T* __restrict__ gs,
+              double* __restrict__ hp) {
+    LBPC_NODE_XYZ
+    init_hprime_node<P, LAYOUT>(a, x, y, z, Qg, h0, gs, hp);
+}
+
+template <int P, int LAYOUT, bool FLOW>
+__global__ void __launch_bounds__(STEP_THREADS)
+k_dist(const __grid_constant__ Args a, const typename Store<P>::T* __restrict__ fs,
+       const typename Store<P>::T* __restrict__ gs, const double* __restrict__ hp,
+       double* __restrict__ Qf, double* __restrict__ Qg) {
+    LBPC_NODE_XYZ
+    dist_node<P, LAYOUT, FLOW>(a, x, y, z, fs, gs, hp, Qf, Qg);
+}
+
+// ---------------------------------------------------------------------------------
+// Host launchers.
+// ---------------------------------------------------------------------------------
+inline dim3 node_block(const Args& a) {
+    const int bx = a.nx >= 128 ? 128 : (a.nx > 32 ? 64 : 32);
+    return dim3(bx, STEP_THREADS / bx, 1);
+}
+inline dim3 node_grid(const Args& a, dim3 blk) {
+    return dim3((a.nx + blk.x - 1) / blk.x, (a.ny + blk.y - 1) / blk.y, a.nz);
+}
+
+template <int P>
+struct Impl {
+    using T = typename Store<P>::T;
+
+    template <int KIND, bool FLOW>
+    static void step_k(const Args& a, const void* fs, void* fd, const void* gs, void* gd,
+                       double* hp, cudaStream_t s) {
+        const dim3 blk = node_block(a), grd = node_grid(a, blk);
+        k_step<P, KIND, FLOW><<<grd, blk, 0, s>>>(a, (const T*)fs, (T*)fd, (const T*)gs, (T*)gd, hp);
+    }
+    static void step(const Args& a, StepKind kind, const void* fs, void* fd, const void* gs,
+                     void* gd, double* hp, cudaStream_t s) {
+        if (a.flow) {
+            if (kind == STEP_PULL) step_k<STEP_PULL, true>(a, fs, fd, gs, gd, hp, s);
+            else if (kind == STEP_AA_EVEN) step_k<STEP_AA_EVEN, true>(a, fs, fd, gs, gd, hp, s);
+            else step_k<STEP_AA_ODD, true>(a, fs, fd, gs, gd, hp, s);
+        } else {
+            if (kind == STEP_PULL) step_k<STEP_PULL, false>(a, fs, fd, gs, gd, hp, s);
+            else if (kind == STEP_AA_EVEN) step_k<STEP_AA_EVEN, false>(a, fs, fd, gs, gd, hp, s);
+            else step_k<STEP_AA_ODD, false>(a, fs, fd, gs, gd, hp, s);
+        }
+    }
+
+    template <int LAYOUT, bool FLOW>
+    static void macro_k(const Args& a, const void* f, const void* g, const double* hp,
+                        const MacroOut& o, cudaStream_t s) {
+        k_macro<P, LAYOUT, FLOW><<<RED_BLOCKS, RED_THREADS, 0, s>>>(a, (const T*)f, (const T*)g, hp, o);
+    }
+    static void macro(const Args& a, Layout lay, const void* f, const void* g, const double* hp,
+                      const MacroOut& o, cudaStream_t s) {
+        if (a.flow) {
+            if (lay == LAYOUT_PULL) macro_k<LAYOUT_PULL, true>(a, f, g, hp, o, s);
+            else if (lay == LAYOUT_AA_NATURAL) macro_k<LAYOUT_AA_NATURAL, true>(a, f, g, hp, o, s);
+            else macro_k<LAYOUT_AA_SWAPPED, true>(a, f, g, hp, o, s);
+        } else {
+            if (lay == LAYOUT_PULL) macro_k<LAYOUT_PULL, false>(a, f, g, hp, o, s);
+            else if (lay == LAYOUT_AA_NATURAL) macro_k<LAYOUT_AA_NATURAL, false>(a, f, g, hp, o, s);
+            else macro_k<LAYOUT_AA_SWAPPED, false>(a, f, g, hp, o, s);
+        }
+    }
+
+    static void init(const Args& a, Layout lay, const double* Qf, const double* Qg,
+                     const double* h0, void* f, void* g, double* hp, cudaStream_t s) {
+        const dim3 blk = node_block(a), grd = node_grid(a, blk);
+        if (lay == LAYOUT_PULL) {
+            if (a.flow) k_init<P, LAYOUT_PULL, true><<<grd, blk, 0, s>>>(a, Qf, Qg, h0, (T*)f, (T*)g);
+            else k_init<P, LAYOUT_PULL, false><<<grd, blk, 0, s>>>(a, Qf, Qg, h0, (T*)f, (T*)g);
+            k_init_hprime<P, LAYOUT_PULL><<<grd, blk, 0, s>>>(a, Qg, h0, (const T*)g, hp);
+        } else {
+            if (a.flow) k_init<P, LAYOUT_AA_NATURAL, true><<<grd, blk, 0, s>>>(a, Qf, Qg, h0, (T*)f, (T*)g);
+            else k_init<P, LAYOUT_AA_NATURAL, false><<<grd, blk, 0, s>>>(a, Qf, Qg, h0, (T*)f, (T*)g);
+            k_init_hprime<P, LAYOUT_AA_NATURAL><<<grd, blk, 0, s>>>(a, Qg, h0, (const T*)g, hp);
+        }
+    }
+
+    template <int LAYOUT>
+    static void dist_k(const Args& a, const void* f, const void* g, const double* hp,
+                       double* Qf, double* Qg, cudaStream_t s) {
+        const dim3 blk = node_block(a), grd = node_grid(a, blk);
+        if (a.flow) k_dist<P, LAYOUT, true><<<grd, blk, 0, s>>>(a, (const T*)f, (const T*)g, hp, Qf, Qg);
+        else k_dist<P, LAYOUT, false><<<grd, blk, 0, s>>>(a, (const T*)f, (const T*)g, hp, Qf, Qg);
+    }
+    static void dist(const Args& a, Layout lay, const void* f, const void* g, const double* hp,
+                     double* Qf, double* Qg, cudaStream_t s) {
+        if (lay == LAYOUT_PULL) dist_k<LAYOUT_PULL>(a, f, g, hp, Qf, Qg, s);
+        else if (lay == LAYOUT_AA_NATURAL) dist_k<LAYOUT_AA_NATURAL>(a, f, g, hp, Qf, Qg, s);
+        else dist_k<LAYOUT_AA_SWAPPED>(a, f, g, hp, Qf, Qg, s);
+    }
+
+    static const Launchers& table() {
+        static const Launchers L = {&step, &macro, &init, &dist, sizeof(T)};
+        return L;
+    }
+};
+#endif  // __CUDACC__
+
+}  // namespace lbpc
