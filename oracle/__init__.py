@@ -22,6 +22,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbpc_oracle.c")
+_SRC_ADJ = os.path.join(_HERE, "lbpc_oracle_adjoint.c")
 _LIB = os.path.join(_HERE, "liblbpc_oracle.so")
 
 L_NAMES = ["chi", "nu", "gbeta", "sigma_chi", "sigma4", "s_nu", "latent", "hs", "hl", "tau_g",
@@ -33,10 +34,11 @@ D_NAMES = ["liquid_vol", "nu_hot", "front_mean", "sum_h", "sum_rho", "step", "nu
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc; returns the path of the shared library."""
     if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= max(
-            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "lbpc_oracle.h"))):
+            os.path.getmtime(_SRC), os.path.getmtime(_SRC_ADJ),
+            os.path.getmtime(os.path.join(_HERE, "lbpc_oracle.h"))):
         return _LIB
     base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-Wall", "-o", _LIB + ".tmp", _SRC,
-            "-lm"]
+            _SRC_ADJ, "-lm"]
     try:
         subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
     except subprocess.CalledProcessError:
@@ -87,6 +89,8 @@ def lib():
         _lib.orc_enth_geq.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, d, d]
         _lib.orc_enth_neq.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, d, d]
         _lib.orc_collide_node.argtypes = [C.c_void_p, d, d, d, d, d]
+        _lib.orc_adjoint.argtypes = [C.c_void_p, C.c_int, C.c_int, d, d, d]
+        _lib.orc_collide_jacobian.argtypes = [C.c_void_p, d, d, d, d]
     return _lib
 
 
@@ -250,6 +254,24 @@ class Oracle:
         lib().orc_collide_node(self._h, _p(f), _p(g), _p(fp), _p(gp), _p(mac))
         return fp, gp, {"h": mac[0], "T": mac[1], "fl": mac[2], "rho": mac[3],
                         "u": mac[4:7].copy(), "F": mac[7:10].copy()}
+
+    def collide_jacobian(self, f, g):
+        """Exact Jacobian of the node collision (complex step) and its L-derivative."""
+        n = 26 if self.flow else 7
+        f = np.ascontiguousarray(f if f is not None else np.zeros(19), dtype=np.float64)
+        g = np.ascontiguousarray(g, dtype=np.float64)
+        J = np.zeros(n * n); dL = np.zeros(26)
+        lib().orc_collide_jacobian(self._h, _p(f), _p(g), _p(J), _p(dL))
+        return J.reshape(n, n), dL[:n]
+
+    def adjoint(self, nsteps: int, face: int = 0):
+        """Run nsteps forward; return J = sum f_l(h_N), dJ/dT_w(face) and dJ/dSt."""
+        A = [self.ny * self.nz] * 2 + [self.nx * self.nz] * 2 + [self.nx * self.ny] * 2
+        J = C.c_double(); dSt = C.c_double(); dTw = np.zeros(A[face])
+        st = lib().orc_adjoint(self._h, int(nsteps), int(face), C.byref(J), _p(dTw), C.byref(dSt))
+        if st != 0:
+            raise RuntimeError("oracle adjoint failed")
+        return J.value, dTw, dSt.value
 
     def update_sampled(self, f, g, idx):
         """New pre-collision populations of nodes ``idx`` after one step from (f, g)."""

@@ -732,3 +732,21 @@ void orc_tables(double *M, double *Minv, double *N, double *Ninv, int *e19, int 
     if (e19) for (int a = 0; a < 19; a++) for (int d = 0; d < 3; d++) e19[a * 3 + d] = E19[a][d];
     if (e7) for (int a = 0; a < 7; a++) for (int d = 0; d < 3; d++) e7[a * 3 + d] = E7[a][d];
 }
+
+/* ---- read-only views for lbpc_oracle_adjoint.c ---- */
+int orc__dims(const orc_state *s, int *nx, int *ny, int *nz) {
+    *nx = s->nx; *ny = s->ny; *nz = s->nz;
+    return 0;
+}
+const orc_params *orc__params(const orc_state *s) { return &s->p; }
+void orc__lattice_raw(const orc_state *s, double *L, double *hs, double *gbeta, double *sigma,
+                      double *lam, const double **Minv, const double **Ninv, const int **opp19,
+                      const int **opp7, const double *const **Tw) {
+    *L = s->L; *hs = s->hs; *gbeta = s->gbeta;
+    memcpy(sigma, s->sigma, sizeof s->sigma);
+    memcpy(lam, s->lam, sizeof s->lam);
+    *Minv = &s->Minv[0][0]; *Ninv = &s->Ninv[0][0];
+    *opp19 = s->opp19; *opp7 = s->opp7;
+    *Tw = (const double *const *)s->Tw;
+}
+double *orc__pop(orc_state *s, int which) { return which == 0 ? s->f : s->g; }

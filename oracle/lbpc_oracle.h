@@ -91,6 +91,15 @@ void orc_enth_neq(const orc_state *s, double h, double T, double fl, const doubl
 void orc_collide_node(const orc_state *s, const double *f, const double *g, double *fpost,
                       double *gpost, double *macro);
 
+/* Reference adjoint (lbpc_oracle_adjoint.c).  Runs nsteps forward from the current
+ * state (advancing it), returns J = sum f_l(h_N), dJ/dT_w for the wall field of `face`
+ * (face-area values) and dJ/dSt.  The state at the call is held fixed. */
+int orc_adjoint(orc_state *s, int nsteps, int face, double *J, double *dJ_dTw, double *dJ_dSt);
+/* Exact Jacobian of the node collision by complex step: J[o*n + i], n = 26 with flow
+ * (f_0..18, g_0..6) or 7 without; dL[o] = d out_o / dL. */
+void orc_collide_jacobian(const orc_state *s, const double *f, const double *g, double *J,
+                          double *dL);
+
 #ifdef __cplusplus
 }
 #endif

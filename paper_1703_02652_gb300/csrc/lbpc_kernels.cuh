@@ -12,6 +12,8 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <cmath>
+
 #include "lbpc_internal.h"
 
 #define LBPC_HD __host__ __device__ __forceinline__
@@ -44,6 +46,38 @@ template <> struct Store<LBPC_BF16S> {
     static LBPC_HD T enc(C v, C s) { return __float2bfloat16_rn(v - s); }
 };
 
+// Exact float -> double by integer operations (subnormal floats, below 1.2e-38, become
+// zero); keeps the conversions off the FP64 pipe, which on GB300 issues a few
+// operations per clock per SM.
+LBPC_HD double f2d_exact(float v) {
+#if defined(__CUDA_ARCH__)
+    const unsigned u = __float_as_uint(v);
+    const unsigned mag = u & 0x7fffffffu;
+    const unsigned long long bits =
+        mag < 0x00800000u ? 0ull
+                          : ((unsigned long long)mag << 29) + (896ull << 52);
+    return __longlong_as_double((long long)(bits | ((unsigned long long)(u >> 31) << 63)));
+#else
+    return (float)v == 0.0f || std::fabs(v) < 1.17549435e-38f ? 0.0 : (double)v;
+#endif
+}
+// double -> float rounding toward zero by integer operations (|v| below 2^-126 gives 0).
+LBPC_HD float d2f_trunc(double v) {
+#if defined(__CUDA_ARCH__)
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    const int ex = (int)((u >> 52) & 0x7ff) - 896;  // float biased exponent
+    const unsigned sign = (unsigned)(u >> 63) << 31;
+    if (ex <= 0) return __uint_as_float(sign);
+    if (ex >= 255) return __uint_as_float(sign | 0x7f800000u);
+    return __uint_as_float(sign | ((unsigned)ex << 23) | (unsigned)((u >> 29) & 0x7fffffu));
+#else
+    const double a = std::fabs(v);
+    if (a < 1.1754943508222875e-38) return std::signbit(v) ? -0.0f : 0.0f;
+    float r = (float)v;
+    if (std::fabs((double)r) > a) r = std::nextafter(r, 0.0f);  // toward zero
+    return r;
+#endif
+}
 template <class C> LBPC_HD const Coef<C>& coef(const Args& a);
 template <> LBPC_HD const Coef<float>& coef<float>(const Args& a) { return a.cf; }
 template <> LBPC_HD const Coef<double>& coef<double>(const Args& a) { return a.cd; }
@@ -60,11 +94,32 @@ template <> LBPC_HD const Coef<double>& coef<double>(const Args& a) { return a.c
     X(1, 1, 0, 0, 2) X(2, -1, 0, 0, 1) X(3, 0, 1, 0, 4) X(4, 0, -1, 0, 3)               \
     X(5, 0, 0, 1, 6) X(6, 0, 0, -1, 5)
 
-// Offsets (in nodes) to the neighbours at x-1 / x+1 etc. with periodic wrap, and
-// whether that neighbour lies behind a wall.
+// Neighbour access policies.  Nb: offsets (in nodes) to the neighbours at x-1 / x+1
+// etc. with periodic wrap, and whether that neighbour lies behind a wall.  NbInterior:
+// a node at least one cell away from every face, where every neighbour is a plain
+// constant offset and no wall rule applies.
 struct Nb {
     int oxm, oxp, oym, oyp, ozm, ozp;
     bool wxm, wxp, wym, wyp, wzm, wzp;
+    // upwind neighbour x - e of velocity e = (EX, EY, EZ): offset and wall test
+    template <int EX, int EY, int EZ>
+    LBPC_HD int off() const {
+        return (EX == 1 ? oxm : EX == -1 ? oxp : 0) + (EY == 1 ? oym : EY == -1 ? oyp : 0) +
+               (EZ == 1 ? ozm : EZ == -1 ? ozp : 0);
+    }
+    template <int EX, int EY, int EZ>
+    LBPC_HD bool wall() const {
+        return (EX == 1 && wxm) || (EX == -1 && wxp) || (EY == 1 && wym) || (EY == -1 && wyp) ||
+               (EZ == 1 && wzm) || (EZ == -1 && wzp);
+    }
+};
+
+struct NbInterior {
+    int sy, sz;  // node strides of y and z
+    template <int EX, int EY, int EZ>
+    LBPC_HD int off() const { return -EX - EY * sy - EZ * sz; }
+    template <int EX, int EY, int EZ>
+    LBPC_HD constexpr bool wall() const { return false; }
 };
 
 LBPC_HD Nb make_nb(const Args& a, int x, int y, int z) {
@@ -85,16 +140,8 @@ LBPC_HD Nb make_nb(const Args& a, int x, int y, int z) {
     return b;
 }
 
-// Upwind neighbour x - e of velocity e = (EX, EY, EZ): offset and wall test.
-template <int EX, int EY, int EZ>
-LBPC_HD int up_off(const Nb& b) {
-    return (EX == 1 ? b.oxm : EX == -1 ? b.oxp : 0) + (EY == 1 ? b.oym : EY == -1 ? b.oyp : 0) +
-           (EZ == 1 ? b.ozm : EZ == -1 ? b.ozp : 0);
-}
-template <int EX, int EY, int EZ>
-LBPC_HD bool up_wall(const Nb& b) {
-    return (EX == 1 && b.wxm) || (EX == -1 && b.wxp) || (EY == 1 && b.wym) ||
-           (EY == -1 && b.wyp) || (EZ == 1 && b.wzm) || (EZ == -1 && b.wzp);
+LBPC_HD bool is_interior(const Args& a, int x, int y, int z) {
+    return x > 0 && x < a.nx - 1 && y > 0 && y < a.ny - 1 && z > 0 && z < a.nz - 1;
 }
 
 // Index of a node inside the temperature field of face `face`.
@@ -125,8 +172,8 @@ LBPC_HD typename Store<P>::T ldv(const typename Store<P>::T* p) {
     return *p;
 }
 
-template <int P, int LAYOUT, bool NC>
-LBPC_HD void gather_f(const Args& a, const Nb& b, int n,
+template <int P, int LAYOUT, bool NC, class NB>
+LBPC_HD void gather_f(const Args& a, const NB& b, int n,
                                          const typename Store<P>::T* fs,
                                          typename Store<P>::C* f) {
     using S = Store<P>;
@@ -140,8 +187,8 @@ LBPC_HD void gather_f(const Args& a, const Nb& b, int n,
         if constexpr (LAYOUT == LAYOUT_AA_NATURAL) {                                    \
             idx = n; slot = q;                                                          \
         } else {                                                                        \
-            const bool w = up_wall<ex, ey, ez>(b);                                      \
-            idx = w ? n : n + up_off<ex, ey, ez>(b);                                    \
+            const bool w = b.template wall<ex, ey, ez>();                                      \
+            idx = w ? n : n + b.template off<ex, ey, ez>();                                    \
             if constexpr (LAYOUT == LAYOUT_PULL) slot = w ? op : q;                      \
             else slot = w ? q : op;                                                     \
         }                                                                               \
@@ -153,8 +200,8 @@ LBPC_HD void gather_f(const Args& a, const Nb& b, int n,
 
 // g_1..6 (g[0] is not gathered: the rest population is the FP64 channel h').  The g
 // lattice holds six planes: population q lives in plane q - 1.
-template <int P, int LAYOUT, bool NC>
-LBPC_HD void gather_g(const Args& a, const Nb& b, int n, int x, int y, int z,
+template <int P, int LAYOUT, bool NC, class NB>
+LBPC_HD void gather_g(const Args& a, const NB& b, int n, int x, int y, int z,
                                          const typename Store<P>::T* gs,
                                          typename Store<P>::C* g) {
     using S = Store<P>;
@@ -166,8 +213,8 @@ LBPC_HD void gather_g(const Args& a, const Nb& b, int n, int x, int y, int z,
         if constexpr (LAYOUT == LAYOUT_AA_NATURAL) {                                    \
             g[q] = S::dec(ldv<P, LAYOUT, NC>(gs + (size_t)(q - 1) * N + n), k.gshift);         \
         } else {                                                                        \
-            const bool w = up_wall<ex, ey, ez>(b);                                      \
-            const int idx = w ? n : n + up_off<ex, ey, ez>(b);                          \
+            const bool w = b.template wall<ex, ey, ez>();                                      \
+            const int idx = w ? n : n + b.template off<ex, ey, ez>();                          \
             int slot;                                                                   \
             if constexpr (LAYOUT == LAYOUT_PULL) slot = w ? op : q;                      \
             else slot = w ? q : op;                                                     \
@@ -183,8 +230,8 @@ LBPC_HD void gather_g(const Args& a, const Nb& b, int n, int x, int y, int z,
 // ---------------------------------------------------------------------------------
 // Scatters of post-collision populations.
 // ---------------------------------------------------------------------------------
-template <int P, int KIND>
-LBPC_HD void scatter_f(const Args& a, const Nb& b, int n,
+template <int P, int KIND, class NB>
+LBPC_HD void scatter_f(const Args& a, const NB& b, int n,
                                           typename Store<P>::T* fd,
                                           const typename Store<P>::C* f) {
     using S = Store<P>;
@@ -199,35 +246,34 @@ LBPC_HD void scatter_f(const Args& a, const Nb& b, int n,
         } else if constexpr (KIND == STEP_AA_EVEN) {                                    \
             fd[(size_t)op * N + n] = v;                                                 \
         } else { /* downwind neighbour x + e is the upwind neighbour of -e */           \
-            const bool w = up_wall<-(ex), -(ey), -(ez)>(b);                             \
+            const bool w = b.template wall<-(ex), -(ey), -(ez)>();                             \
             if (w) fd[(size_t)op * N + n] = v;                                          \
-            else fd[(size_t)q * N + n + up_off<-(ex), -(ey), -(ez)>(b)] = v;            \
+            else fd[(size_t)q * N + n + b.template off<-(ex), -(ey), -(ez)>()] = v;            \
         }                                                                               \
     }
     LBPC_Q19(LBPC_SF)
 #undef LBPC_SF
 }
 
-// Returns sum over a of the stored (rounded) g*_a, in FP64.
-template <int P, int KIND>
-LBPC_HD double scatter_g(const Args& a, const Nb& b, int n, int x, int y,
-                                            int z, typename Store<P>::T* gd,
-                                            const typename Store<P>::C* g) {
+// Stores g*_1..6 and replaces g[a] by the value as stored (rounded to the storage
+// precision), which is what the downwind neighbours will read.
+template <int P, int KIND, class NB>
+LBPC_HD void scatter_g(const Args& a, const NB& b, int n, int x, int y, int z,
+                       typename Store<P>::T* gd, typename Store<P>::C* g) {
     using S = Store<P>;
     using C = typename S::C;
     const Coef<C>& k = coef<C>(a);
     const size_t N = (size_t)a.N;
-    double sum = 0.0;
 #define LBPC_SG(q, ex, ey, ez, op)                                                       \
     {                                                                                   \
         const auto v = S::enc(g[q], k.gshift);                                          \
-        sum += (double)S::dec(v, k.gshift);                                             \
+        g[q] = S::dec(v, k.gshift);                                                     \
         if constexpr (KIND == STEP_PULL) {                                              \
             gd[(size_t)(q - 1) * N + n] = v;                                                  \
         } else if constexpr (KIND == STEP_AA_EVEN) {                                    \
             gd[(size_t)(op - 1) * N + n] = v;                                                 \
         } else {                                                                        \
-            const bool w = up_wall<-(ex), -(ey), -(ez)>(b);                             \
+            const bool w = b.template wall<-(ex), -(ey), -(ez)>();                             \
             if (w) {                                                                    \
                 auto vb = v;                                                            \
                 if (a.wall_iso[op - 1])                                                 \
@@ -235,13 +281,12 @@ LBPC_HD double scatter_g(const Args& a, const Nb& b, int n, int x, int y,
                                 k.gshift);                                              \
                 gd[(size_t)(op - 1) * N + n] = vb;                                            \
             } else {                                                                    \
-                gd[(size_t)(q - 1) * N + n + up_off<-(ex), -(ey), -(ez)>(b)] = v;             \
+                gd[(size_t)(q - 1) * N + n + b.template off<-(ex), -(ey), -(ez)>()] = v;             \
             }                                                                           \
         }                                                                               \
     }
     LBPC_Q7(LBPC_SG)
 #undef LBPC_SG
-    return sum;
 }
 
 // ---------------------------------------------------------------------------------
@@ -249,10 +294,14 @@ LBPC_HD double scatter_g(const Args& a, const Nb& b, int n, int x, int y,
 // ---------------------------------------------------------------------------------
 
 // Eq. 2 inverted (h = C_p T + f_l L; solid for h <= h_s, liquid for h >= h_s + L, mushy
-// at T_m in between).  The cancelling subtraction h - h_s is done in FP64.
+// at T_m in between), from the FP64 enthalpy excess e = h - h_s that the rest channel
+// carries, so that the cancelling subtraction near the melting point is exact.
+LBPC_HD float to_compute(double v, float) { return d2f_trunc(v); }
+LBPC_HD double to_compute(double v, double) { return v; }
+
 template <class C>
-LBPC_HD void invert_h(const Args& a, const Coef<C>& k, double h, C& T, C& fl) {
-    const C d = (C)(h - a.hs);
+LBPC_HD void invert_excess(const Coef<C>& k, double e, C& T, C& fl) {
+    const C d = to_compute(e, C(0));
     if (d <= C(0)) {
         fl = C(0);
         T = k.Tm + d * k.Cps_inv;
@@ -427,16 +476,42 @@ LBPC_HD void collide_enth(C* g, const Coef<C>& k, C T, C fl, C ux, C uy,
     g[6] = e6 + d6 - (-hc * m3 + c36 - D);
 }
 
-template <class C>
-LBPC_HD double hsum6(double hprime, const C* g) {
-    double h = hprime;
-    h += (double)g[1];
-    h += (double)g[2];
-    h += (double)g[3];
-    h += (double)g[4];
-    h += (double)g[5];
-    h += (double)g[6];
-    return h;
+// The rest channel stores e' = h' - h_s in FP64, so that e = h - h_s = e' + sum_{a>=1} g_a.
+// With 32/16-bit populations the six values are summed exactly in FP32 (Knuth's TwoSum:
+// s + err == a + b) into an unevaluated pair hi + lo, and only the pair enters FP64:
+// four FP64 additions and five conversions per node instead of a dozen of each.
+LBPC_HD void two_sum(float a, float b, float& s, float& err) {
+    s = a + b;
+    const float bb = s - a;
+    err = (a - (s - bb)) + (b - bb);
+}
+LBPC_HD void sum6_pair(const float* g, float& hi, float& lo) {
+    float e;
+    hi = g[1];
+    lo = 0.0f;
+    two_sum(hi, g[2], hi, e); lo += e;
+    two_sum(hi, g[3], hi, e); lo += e;
+    two_sum(hi, g[4], hi, e); lo += e;
+    two_sum(hi, g[5], hi, e); lo += e;
+    two_sum(hi, g[6], hi, e); lo += e;
+}
+// e' + sum g_a
+LBPC_HD double excess_plus(double ep, const float* g) {
+    float hi, lo;
+    sum6_pair(g, hi, lo);
+    return (ep + f2d_exact(hi)) + f2d_exact(lo);
+}
+LBPC_HD double excess_plus(double ep, const double* g) {
+    return ep + g[1] + g[2] + g[3] + g[4] + g[5] + g[6];
+}
+// e - sum g_a
+LBPC_HD double excess_minus(double e, const float* g) {
+    float hi, lo;
+    sum6_pair(g, hi, lo);
+    return (e - f2d_exact(hi)) - f2d_exact(lo);
+}
+LBPC_HD double excess_minus(double e, const double* g) {
+    return e - g[1] - g[2] - g[3] - g[4] - g[5] - g[6];
 }
 
 // ---------------------------------------------------------------------------------
@@ -459,25 +534,35 @@ LBPC_HD void step_node(const Args& a, int x, int y, int z, const typename Store<
     using C = typename S::C;
     const Coef<C>& k = coef<C>(a);
     const int n = x + a.nx * (y + a.ny * z);
-    const Nb b = make_nb(a, x, y, z);
     constexpr int LAYOUT = KindLayout<KIND>::value;
     constexpr bool NC = KIND == STEP_PULL;  // read-only path only when src != dst
+    const bool interior = is_interior(a, x, y, z);
+    const NbInterior bi{a.nx, a.nx * a.ny};
+    const Nb b = make_nb(a, x, y, z);
 
     C f[19], g[7];
-    if constexpr (FLOW) gather_f<P, LAYOUT, NC>(a, b, n, fs, f);
-    gather_g<P, LAYOUT, NC>(a, b, n, x, y, z, gs, g);
-    const double h = hsum6(hp[n], g);
+    if (interior) {
+        if constexpr (FLOW) gather_f<P, LAYOUT, NC>(a, bi, n, fs, f);
+        gather_g<P, LAYOUT, NC>(a, bi, n, x, y, z, gs, g);
+    } else {
+        if constexpr (FLOW) gather_f<P, LAYOUT, NC>(a, b, n, fs, f);
+        gather_g<P, LAYOUT, NC>(a, b, n, x, y, z, gs, g);
+    }
+    const double e = excess_plus(hp[n], g);  // h - h_s
 
     C T, fl;
-    invert_h(a, k, h, T, fl);
+    invert_excess(k, e, T, fl);
     C ux = C(0), uy = C(0), uz = C(0);
-    if constexpr (FLOW) {
-        collide_flow(f, k, T, fl, ux, uy, uz);
-        scatter_f<P, KIND>(a, b, n, fd, f);
-    }
+    if constexpr (FLOW) collide_flow(f, k, T, fl, ux, uy, uz);
     collide_enth(g, k, T, fl, ux, uy, uz);
-    const double sout = scatter_g<P, KIND>(a, b, n, x, y, z, gd, g);
-    hp[n] = h - sout;
+    if (interior) {
+        if constexpr (FLOW) scatter_f<P, KIND>(a, bi, n, fd, f);
+        scatter_g<P, KIND>(a, bi, n, x, y, z, gd, g);
+    } else {
+        if constexpr (FLOW) scatter_f<P, KIND>(a, b, n, fd, f);
+        scatter_g<P, KIND>(a, b, n, x, y, z, gd, g);
+    }
+    hp[n] = excess_minus(e, g);
 }
 
 // Macroscopic state of node n and its contributions to the diagnostics sums
@@ -494,9 +579,10 @@ LBPC_HD void macro_node(const Args& a, int n, const typename Store<P>::T* fs,
     C f[19], g[7];
     if constexpr (FLOW) gather_f<P, LAYOUT, true>(a, b, n, fs, f);
     gather_g<P, LAYOUT, true>(a, b, n, x, y, z, gs, g);
-    const double h = hsum6(hp[n], g);
+    const double e = excess_plus(hp[n], g);
+    const double h = a.hs + e;
     C T, fl;
-    invert_h(a, k, h, T, fl);
+    invert_excess(k, e, T, fl);
     C rho = C(0), ux = C(0), uy = C(0), uz = C(0);
     if constexpr (FLOW) {
         C jx, jy, jz, Fx, Fy, Fz;
@@ -538,7 +624,7 @@ LBPC_HD double state_g(const Args& a, const Coef<C>& k, const double* Qg, const 
                        int q, int m) {
     if (Qg) return Qg[(size_t)q * a.N + m];
     C T, fl;
-    invert_h(a, k, h0[m], T, fl);
+    invert_excess(k, h0[m] - a.hs, T, fl);
     return (double)(k.wa_cref * T);
 }
 
@@ -560,9 +646,9 @@ LBPC_HD void init_node(const Args& a, int x, int y, int z, const double* Qf, con
             double v;                                                                   \
             if constexpr (LAYOUT == LAYOUT_AA_NATURAL) v = state_f<C>(Qf, N, q, n);     \
             else {                                                                      \
-                const bool w = up_wall<-(ex), -(ey), -(ez)>(b);                         \
+                const bool w = b.template wall<-(ex), -(ey), -(ez)>();                         \
                 v = w ? state_f<C>(Qf, N, op, n)                                        \
-                      : state_f<C>(Qf, N, q, n + up_off<-(ex), -(ey), -(ez)>(b));       \
+                      : state_f<C>(Qf, N, q, n + b.template off<-(ex), -(ey), -(ez)>());       \
             }                                                                           \
             fd[(size_t)q * N + n] = S::enc((C)v, fshift(k, q));                         \
         }
@@ -574,13 +660,13 @@ LBPC_HD void init_node(const Args& a, int x, int y, int z, const double* Qf, con
         double v;                                                                       \
         if constexpr (LAYOUT == LAYOUT_AA_NATURAL) v = state_g(a, k, Qg, h0, q, n);     \
         else {                                                                          \
-            const bool w = up_wall<-(ex), -(ey), -(ez)>(b);                             \
+            const bool w = b.template wall<-(ex), -(ey), -(ez)>();                             \
             if (w) {                                                                    \
                 v = state_g(a, k, Qg, h0, op, n);                                       \
                 if (a.wall_iso[op - 1])                                                 \
                     v = (double)k.wT_cref * a.Tw[op - 1][face_index(a, op - 1, x, y, z)] - v; \
             } else {                                                                    \
-                v = state_g(a, k, Qg, h0, q, n + up_off<-(ex), -(ey), -(ez)>(b));       \
+                v = state_g(a, k, Qg, h0, q, n + b.template off<-(ex), -(ey), -(ez)>());       \
             }                                                                           \
         }                                                                               \
         gd[(size_t)(q - 1) * N + n] = S::enc((C)v, k.gshift);                                 \
@@ -589,7 +675,7 @@ LBPC_HD void init_node(const Args& a, int x, int y, int z, const double* Qf, con
 #undef LBPC_IG
 }
 
-// h' = h - sum_a g_a(gathered), so that the stored state reproduces h.
+// e' = h - h_s - sum_a g_a(gathered), so that the stored state reproduces h.
 template <int P, int LAYOUT>
 LBPC_HD void init_hprime_node(const Args& a, int x, int y, int z, const double* Qg,
                               const double* h0, const typename Store<P>::T* gs, double* hp) {
@@ -605,12 +691,10 @@ LBPC_HD void init_hprime_node(const Args& a, int x, int y, int z, const double* 
     }
     C g[7];
     gather_g<P, LAYOUT, true>(a, b, n, x, y, z, gs, g);
-    double s = 0.0;
-    for (int q = 1; q < 7; q++) s += (double)g[q];
-    hp[n] = h - s;
+    hp[n] = excess_minus(h - a.hs, g);
 }
 
-// Pre-collision populations of node (x, y, z) in FP64 (g_0 = h').
+// Pre-collision populations of node (x, y, z) in FP64 (g_0 = h' = h_s + e').
 template <int P, int LAYOUT, bool FLOW>
 LBPC_HD void dist_node(const Args& a, int x, int y, int z, const typename Store<P>::T* fs,
                        const typename Store<P>::T* gs, const double* hp, double* Qf, double* Qg) {
@@ -620,7 +704,7 @@ LBPC_HD void dist_node(const Args& a, int x, int y, int z, const typename Store<
     const size_t N = (size_t)a.N;
     C g[7];
     gather_g<P, LAYOUT, true>(a, b, n, x, y, z, gs, g);
-    Qg[n] = hp[n];
+    Qg[n] = a.hs + hp[n];
     for (int q = 1; q < 7; q++) Qg[(size_t)q * N + n] = (double)g[q];
     if constexpr (FLOW) {
         if (Qf) {

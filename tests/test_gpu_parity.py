@@ -155,17 +155,22 @@ def test_one_step_from_random_state(precision, streaming, flow_model):
         o.set_distributions(f1.cpu().numpy() if f1 is not None else None, g1.cpu().numpy())
 
 
-def test_aa_and_pull_agree_bitwise():
+@pytest.mark.parametrize("precision,tol", [(inp.FP64, 1e-13), (inp.FP32, 2e-6), (inp.FP16, 1e-3)])
+def test_aa_and_pull_agree(precision, tol):
+    """The two streaming schemes compute the same arithmetic on the same values; they
+    differ only where the compiler contracts a multiply-add differently in the two
+    kernel instantiations (FP32 rounding), which in FP16 storage can move a stored value
+    by one FP16 ulp (2.4e-4 at 0.25)."""
     shape = (16, 12, 10)
     res = {}
     for streaming in (inp.PULL, inp.AA):
-        p = inp.Params(precision=inp.FP32, streaming=streaming, Ra=5e4, Pr=0.7, St=1.0)
+        p = inp.Params(precision=precision, streaming=streaming, Ra=5e4, Pr=0.7, St=1.0)
         g = LBPC(shape, p)
         g.set_initial_h(np.linspace(-0.2, 1.5, int(np.prod(shape))))
         g.step(41)
         res[streaming] = _np(g.fields())
     for k in KEYS:
-        assert np.array_equal(res[inp.PULL][k], res[inp.AA][k]), k
+        assert np.abs(res[inp.PULL][k] - res[inp.AA][k]).max() <= tol, k
 
 
 @pytest.mark.parametrize("precision,tol", [(inp.FP32, 1e-5), (inp.FP16, 1e-3), (inp.BF16, 1e-2)])
