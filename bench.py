@@ -152,6 +152,47 @@ def cpu_baseline(seconds=15.0, min_steps=2):
                       f"{SAMPLE_SHAPE[2]} slab of the 256^3 cavity (same lattice constants)"}
 
 
+def adjoint_ratio(p, shape, h0, steps=200, intervals=(50, 100, 200)):
+    """Wall time of the adjoint (forward with checkpoints, then backward: segment
+    recompute with the macroscopic tape + reverse sweep) over the plain forward, same
+    steps, same state; CUDA events on the handle's stream."""
+    import torch
+    from paper_1703_02652_gb300 import LBPC
+
+    g = LBPC(shape, p.replace(report_every=0))
+    g.set_initial_h(h0)
+    g.step(5)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    torch.cuda.synchronize()
+    ev[0].record(g.stream)
+    g.step(steps)
+    ev[1].record(g.stream)
+    torch.cuda.synchronize()
+    t_fwd = ev[0].elapsed_time(ev[1])
+    out = {"lattice": list(shape), "steps": steps, "forward_ms_per_step": t_fwd / steps,
+           "backward_over_forward": {}, "total_over_forward": {}, "workspace_gb": {}}
+    for k in intervals:
+        g.set_initial_h(h0)
+        g.step(5)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ev[0].record(g.stream)
+        g.adjoint_forward(steps, k)  # synchronises to return J
+        ev[1].record(g.stream)
+        g.adjoint_backward(0)
+        ev[2].record(g.stream)
+        torch.cuda.synchronize()
+        t_af, t_ab = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+        out["backward_over_forward"][str(k)] = t_ab / t_fwd
+        out["total_over_forward"][str(k)] = (t_af + t_ab) / t_fwd
+        out["workspace_gb"][str(k)] = g._adj_ws.numel() / 1e9
+        g.release_adjoint_workspace()
+        torch.cuda.empty_cache()
+    del g
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -290,6 +331,8 @@ def run_ours(args):
                 "what": "create + initial h from pinned host + K steps + T, f_l and scalars "
                         "to host, per-step bytes = totals / K"},
     }
+    if world == 1 and not args.no_adjoint and streaming == inp.PULL:
+        line["adjoint"] = adjoint_ratio(p, w.shape, h0)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))
@@ -308,6 +351,7 @@ def main():
     ap.add_argument("--streaming", default="pull", choices=["pull", "aa"])
     ap.add_argument("--lattice", type=int, default=256, help="cavity edge (profiling only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     assert args.warmup >= 3, "at least 3 warm-up steps"
     if args.impl == "reference":

@@ -186,6 +186,34 @@ size_t lbpc_state_bytes(const lbpc_handle *h);
 lbpc_status lbpc_save(lbpc_handle *h, void *host_buf, size_t bytes);
 lbpc_status lbpc_load(lbpc_handle *h, const void *host_buf, size_t bytes);
 
+/*
+ * Adjoint (hand-written reverse mode of the coupled step; not in the paper, which has
+ * no gradients).  Objective J = sum over nodes of f_l(h_N), the liquid volume after
+ * nsteps steps from the state held when lbpc_adjoint_forward is called; that state is a
+ * fixed input.  Gradients: dJ/dT_w of the per-node temperature field of one isothermal
+ * face (face-area values, layout of lbpc_set_wall_temperature) and dJ/dSt, where St
+ * enters through L = C_p,l (Th - Tm) / St (Eq. 2, 64).  Derivatives at the kinks of the
+ * Eq. 2 inversion are those of the branch the forward took.
+ *
+ * Memory stays bounded by checkpointing: the forward saves the state every ckpt_every
+ * steps; the backward recomputes each segment writing a per-step macroscopic tape
+ * (h - h_s in FP64, rho and j in the compute precision: 24 B per node and step in FP32)
+ * and sweeps it backwards.  The adjoint populations are kept in the compute precision;
+ * the parameter gradients accumulate in FP64.  Pull streaming only (LBPC_ERR_STATE
+ * otherwise).  dev_ws: device, 256-byte aligned, >= lbpc_adjoint_workspace_bytes().
+ *
+ * lbpc_adjoint_forward advances the handle by nsteps and returns J (host);
+ * lbpc_adjoint_backward (no stepping in between) returns the gradients (host) and leaves
+ * the handle at the final state; lbpc_adjoint does both.
+ */
+size_t lbpc_adjoint_workspace_bytes(const lbpc_handle *h, int nsteps, int ckpt_every);
+lbpc_status lbpc_adjoint_forward(lbpc_handle *h, int nsteps, int ckpt_every, void *dev_ws,
+                                 size_t ws_bytes, double *J_host);
+lbpc_status lbpc_adjoint_backward(lbpc_handle *h, int face, double *dJ_dTw_host,
+                                  double *dJ_dSt_host);
+lbpc_status lbpc_adjoint(lbpc_handle *h, int nsteps, int ckpt_every, void *dev_ws, size_t ws_bytes,
+                         int face, double *J_host, double *dJ_dTw_host, double *dJ_dSt_host);
+
 long long lbpc_step_count(const lbpc_handle *h);
 /* Number of kernels this handle has launched since it was created. */
 long long lbpc_launch_count(const lbpc_handle *h);

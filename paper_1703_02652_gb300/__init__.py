@@ -6,3 +6,4 @@ Li & He (Sec. 2.2-2.5) -- is hand-written CUDA in ``csrc/`` behind the C ABI of
 """
 from .binding import LbpcError, lib  # noqa: F401
 from .lbpc import LBPC  # noqa: F401
+from .autograd import LiquidVolume, liquid_volume  # noqa: F401

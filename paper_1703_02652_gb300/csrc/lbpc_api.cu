@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <string>
@@ -60,6 +61,20 @@ WsLayout ws_layout(int nx, int ny, int nz, const lbpc_params* p) {
     w.stage = off; off = align_up(off + 8 * N);
     w.total = off;
     return w;
+}
+
+// Fixed-order sum of n partials into out[0] (one block).
+__global__ void __launch_bounds__(256) k_sum(const double* __restrict__ p, int n, double* out) {
+    __shared__ double sh[256];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += p[i];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int st = 128; st > 0; st >>= 1) {
+        if ((int)threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0];
 }
 
 __global__ void k_fill(double* p, double v, int n) {
@@ -131,6 +146,19 @@ struct lbpc_handle {
     long long hist_count;
     long long launches;
     bool diverged;
+    struct Adjoint {
+        bool ready = false;
+        char* ws = nullptr;
+        int nsteps = 0, k = 0, nseg = 0;
+        long long end_step = 0;
+        size_t ckpt_bytes = 0, off_f = 0, off_g = 0, off_hp = 0;
+        char* ckpt = nullptr;
+        double* tape_e = nullptr;
+        void* tape_m = nullptr;
+        void* lam[2] = {nullptr, nullptr};
+        double *gtw = nullptr, *Lpart = nullptr, *Jpart = nullptr, *red = nullptr;
+        int nblocks = 0;
+    } adj;
     Args args;
     std::string err;
 };
@@ -574,6 +602,188 @@ void lbpc_destroy(lbpc_handle* h) {
     if (cudaGetDevice(&cur) == cudaSuccess && cur != h->device) cudaSetDevice(h->device);
     cudaStreamSynchronize(h->stream);
     delete h;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------
+// Adjoint (reverse mode with checkpointing).
+// ---------------------------------------------------------------------------------
+namespace {
+
+struct AdjLayout {
+    size_t ckpt_bytes, off_f, off_g, off_hp, ckpt, tape_e, tape_m, lam0, lam1, gtw, Lpart, Jpart,
+        red, total;
+    int nseg, nblocks;
+};
+
+AdjLayout adj_layout(const lbpc_handle* h, int nsteps, int k) {
+    AdjLayout L{};
+    const size_t N = (size_t)h->N, S = h->L->store_bytes, Cb = h->L->compute_bytes;
+    const bool flow = h->p.flow_model != LBPC_FLOW_NONE;
+    L.nseg = (nsteps + k - 1) / k;
+    L.off_f = 0;
+    L.off_g = align_up(flow ? 19 * N * S : 0);
+    L.off_hp = L.off_g + align_up(6 * N * S);
+    L.ckpt_bytes = L.off_hp + align_up(8 * N);
+    size_t off = 0;
+    L.ckpt = off; off += (size_t)(L.nseg + 1) * L.ckpt_bytes;
+    L.tape_e = off; off = align_up(off + (size_t)k * 8 * N);
+    L.tape_m = off; off = align_up(off + (flow ? (size_t)k * 4 * N * Cb : 0));
+    const size_t lam = (size_t)(flow ? 26 : 7) * N * Cb;
+    L.lam0 = off; off = align_up(off + lam);
+    L.lam1 = off; off = align_up(off + lam);
+    size_t amax = 0;
+    for (int f = 0; f < 6; f++) amax = std::max(amax, (size_t)face_area(h->nx, h->ny, h->nz, f));
+    L.gtw = off; off = align_up(off + 8 * amax);
+    L.nblocks = node_grid_blocks(h->nx, h->ny, h->nz);
+    L.Lpart = off; off = align_up(off + 8 * (size_t)L.nblocks);
+    L.Jpart = off; off = align_up(off + 8 * (size_t)L.nblocks);
+    L.red = off; off = align_up(off + 8 * 4);
+    L.total = off;
+    return L;
+}
+
+lbpc_status save_state(lbpc_handle* h, char* dst) {
+    auto& A = h->adj;
+    const size_t N = (size_t)h->N, S = h->L->store_bytes;
+    if (h->p.flow_model != LBPC_FLOW_NONE)
+        LBPC_CK(h, cudaMemcpyAsync(dst + A.off_f, h->f[h->cur], 19 * N * S, cudaMemcpyDeviceToDevice, h->stream));
+    LBPC_CK(h, cudaMemcpyAsync(dst + A.off_g, h->g[h->cur], 6 * N * S, cudaMemcpyDeviceToDevice, h->stream));
+    LBPC_CK(h, cudaMemcpyAsync(dst + A.off_hp, h->hp, 8 * N, cudaMemcpyDeviceToDevice, h->stream));
+    return LBPC_OK;
+}
+
+lbpc_status restore_state(lbpc_handle* h, const char* src) {
+    auto& A = h->adj;
+    const size_t N = (size_t)h->N, S = h->L->store_bytes;
+    h->cur = 0;
+    if (h->p.flow_model != LBPC_FLOW_NONE)
+        LBPC_CK(h, cudaMemcpyAsync(h->f[0], src + A.off_f, 19 * N * S, cudaMemcpyDeviceToDevice, h->stream));
+    LBPC_CK(h, cudaMemcpyAsync(h->g[0], src + A.off_g, 6 * N * S, cudaMemcpyDeviceToDevice, h->stream));
+    LBPC_CK(h, cudaMemcpyAsync(h->hp, src + A.off_hp, 8 * N, cudaMemcpyDeviceToDevice, h->stream));
+    return LBPC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lbpc_adjoint_workspace_bytes(const lbpc_handle* h, int nsteps, int ckpt_every) {
+    if (!h || nsteps < 1 || ckpt_every < 1) return 0;
+    return adj_layout(h, nsteps, ckpt_every).total;
+}
+
+lbpc_status lbpc_adjoint_forward(lbpc_handle* h, int nsteps, int ckpt_every, void* dev_ws,
+                                 size_t ws_bytes, double* J_host) {
+    if (!h) return LBPC_ERR_PARAM;
+    if (nsteps < 1 || ckpt_every < 1) return fail(h, LBPC_ERR_PARAM, "nsteps and ckpt_every must be >= 1");
+    if (h->p.streaming != LBPC_PULL) return fail(h, LBPC_ERR_STATE, "the adjoint needs pull streaming");
+    if (h->diverged) return fail(h, LBPC_ERR_STATE, "state diverged");
+    const AdjLayout L = adj_layout(h, nsteps, ckpt_every);
+    if (!dev_ws || ((uintptr_t)dev_ws) % kAlign != 0 || ws_bytes < L.total)
+        return fail(h, LBPC_ERR_WORKSPACE, "adjoint workspace missing, misaligned or smaller than lbpc_adjoint_workspace_bytes()");
+    lbpc_status s = set_device(h);
+    if (s != LBPC_OK) return s;
+    auto& A = h->adj;
+    char* w = (char*)dev_ws;
+    A.ready = false;
+    A.ws = w;
+    A.nsteps = nsteps;
+    A.k = ckpt_every;
+    A.nseg = L.nseg;
+    A.nblocks = L.nblocks;
+    A.ckpt_bytes = L.ckpt_bytes;
+    A.off_f = L.off_f; A.off_g = L.off_g; A.off_hp = L.off_hp;
+    A.ckpt = w + L.ckpt;
+    A.tape_e = (double*)(w + L.tape_e);
+    A.tape_m = w + L.tape_m;
+    A.lam[0] = w + L.lam0;
+    A.lam[1] = w + L.lam1;
+    A.gtw = (double*)(w + L.gtw);
+    A.Lpart = (double*)(w + L.Lpart);
+    A.Jpart = (double*)(w + L.Jpart);
+    A.red = (double*)(w + L.red);
+    // forward with a checkpoint at the start of every segment and one of the final state
+    s = save_state(h, A.ckpt);
+    if (s != LBPC_OK) return s;
+    for (int i = 0; i < nsteps; i++) {
+        h->L->step(h->args, STEP_PULL, h->f[h->cur], h->f[1 - h->cur], h->g[h->cur], h->g[1 - h->cur],
+                   h->hp, h->stream);
+        h->cur = 1 - h->cur;
+        h->step++;
+        h->launches++;
+        if ((i + 1) % ckpt_every == 0 && i + 1 < nsteps) {
+            s = save_state(h, A.ckpt + (size_t)((i + 1) / ckpt_every) * A.ckpt_bytes);
+            if (s != LBPC_OK) return s;
+        }
+    }
+    s = save_state(h, A.ckpt + (size_t)A.nseg * A.ckpt_bytes);
+    if (s != LBPC_OK) return s;
+    // seed lambda_N = d f_l / dh (and J = sum f_l, the direct dJ/dL part)
+    h->L->adj_seed(h->args, h->g[h->cur], h->hp, A.lam[0], A.Lpart, A.Jpart, h->stream);
+    k_sum<<<1, 256, 0, h->stream>>>(A.Jpart, A.nblocks, A.red);
+    h->launches += 2;
+    LBPC_CK(h, cudaGetLastError());
+    double J = 0.0;
+    LBPC_CK(h, cudaMemcpyAsync(&J, A.red, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    LBPC_CK(h, cudaStreamSynchronize(h->stream));
+    if (J_host) *J_host = J;
+    A.end_step = h->step;
+    A.ready = true;
+    return LBPC_OK;
+}
+
+lbpc_status lbpc_adjoint_backward(lbpc_handle* h, int face, double* dJ_dTw_host, double* dJ_dSt_host) {
+    if (!h) return LBPC_ERR_PARAM;
+    if (face < 0 || face > 5) return fail(h, LBPC_ERR_PARAM, "face must be 0..5");
+    auto& A = h->adj;
+    if (!A.ready || h->step != A.end_step)
+        return fail(h, LBPC_ERR_STATE, "call lbpc_adjoint_forward first (and do not step in between)");
+    lbpc_status s = set_device(h);
+    if (s != LBPC_OK) return s;
+    const size_t N = (size_t)h->N, Cb = h->L->compute_bytes;
+    LBPC_CK(h, cudaMemsetAsync(A.gtw, 0, 8 * face_area(h->nx, h->ny, h->nz, face), h->stream));
+    int cl = 0;
+    for (int seg = A.nseg - 1; seg >= 0; seg--) {
+        const int start = seg * A.k, len = std::min(A.k, A.nsteps - start);
+        s = restore_state(h, A.ckpt + (size_t)seg * A.ckpt_bytes);
+        if (s != LBPC_OK) return s;
+        for (int t = 0; t < len; t++) {  // recompute the segment, writing the tape
+            h->L->step_tape(h->args, h->f[h->cur], h->f[1 - h->cur], h->g[h->cur], h->g[1 - h->cur],
+                            h->hp, A.tape_e + (size_t)t * N, (char*)A.tape_m + (size_t)t * 4 * N * Cb,
+                            h->stream);
+            h->cur = 1 - h->cur;
+        }
+        for (int t = len - 1; t >= 0; t--) {  // reverse sweep
+            h->L->adj_reverse(h->args, A.lam[cl], A.lam[1 - cl], A.tape_e + (size_t)t * N,
+                              (char*)A.tape_m + (size_t)t * 4 * N * Cb, face, A.gtw, A.Lpart, h->stream);
+            cl = 1 - cl;
+        }
+        h->launches += 2 * len;
+    }
+    k_sum<<<1, 256, 0, h->stream>>>(A.Lpart, A.nblocks, A.red + 1);
+    h->launches++;
+    LBPC_CK(h, cudaGetLastError());
+    s = restore_state(h, A.ckpt + (size_t)A.nseg * A.ckpt_bytes);  // back to the final state
+    if (s != LBPC_OK) return s;
+    double dJdL = 0.0;
+    LBPC_CK(h, cudaMemcpyAsync(&dJdL, A.red + 1, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (dJ_dTw_host)
+        LBPC_CK(h, cudaMemcpyAsync(dJ_dTw_host, A.gtw, 8 * face_area(h->nx, h->ny, h->nz, face),
+                                   cudaMemcpyDeviceToHost, h->stream));
+    LBPC_CK(h, cudaStreamSynchronize(h->stream));
+    // L = C_p,l dT / St
+    if (dJ_dSt_host) *dJ_dSt_host = dJdL * (-h->p.Cp_l * h->d.dT / (h->p.St * h->p.St));
+    A.ready = false;
+    return LBPC_OK;
+}
+
+lbpc_status lbpc_adjoint(lbpc_handle* h, int nsteps, int ckpt_every, void* dev_ws, size_t ws_bytes,
+                         int face, double* J_host, double* dJ_dTw_host, double* dJ_dSt_host) {
+    lbpc_status s = lbpc_adjoint_forward(h, nsteps, ckpt_every, dev_ws, ws_bytes, J_host);
+    if (s != LBPC_OK) return s;
+    return lbpc_adjoint_backward(h, face, dJ_dTw_host, dJ_dSt_host);
 }
 
 }  // extern "C"

@@ -64,8 +64,27 @@ struct Launchers {
     // pre-collision populations in FP64 (f: 19N or null, g: 7N)
     void (*dist)(const Args&, Layout, const void* f, const void* g, const double* hp,
                  double* Qf, double* Qg, cudaStream_t);
-    size_t store_bytes;  // bytes of one stored population value
+    // adjoint: pull step that also writes the macroscopic tape (e: N doubles; rho, j:
+    // 4N compute-precision values), seed of lambda at the final state, one reverse step
+    void (*step_tape)(const Args&, const void* fs, void* fd, const void* gs, void* gd,
+                      double* hp, double* tape_e, void* tape_m, cudaStream_t);
+    void (*adj_seed)(const Args&, const void* gs, const double* hp, void* lam, double* Lpart,
+                     double* Jpart, cudaStream_t);
+    void (*adj_reverse)(const Args&, const void* lin, void* lout, const double* tape_e,
+                        const void* tape_m, int wface, double* gtw, double* Lpart, cudaStream_t);
+    size_t store_bytes;    // bytes of one stored population value
+    size_t compute_bytes;  // bytes of one compute-precision value (adjoint, tape)
 };
+
+// node grid of the per-node kernels (blocks of 128 threads along x, then y)
+inline dim3 node_block_dims(int nx) {
+    const int bx = nx >= 128 ? 128 : (nx > 32 ? 64 : 32);
+    return dim3(bx, 128 / bx, 1);
+}
+inline int node_grid_blocks(int nx, int ny, int nz) {
+    const dim3 b = node_block_dims(nx);
+    return ((nx + b.x - 1) / b.x) * ((ny + b.y - 1) / b.y) * nz;
+}
 
 const Launchers& launchers_f64();
 const Launchers& launchers_f32();

@@ -78,6 +78,41 @@ LBPC_HD float d2f_trunc(double v) {
     return r;
 #endif
 }
+// Pairs of consecutive nodes along x: vector types and codecs of two values.
+template <class T> struct Vec2;
+template <> struct Vec2<double> { using type = double2; };
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<__half> { using type = __half2; };
+template <> struct Vec2<__nv_bfloat16> { using type = __nv_bfloat162; };
+
+template <int P> struct Pair;
+template <> struct Pair<LBPC_FP64> {
+    static LBPC_HD void dec(double2 v, double, double& a, double& b) { a = v.x; b = v.y; }
+    static LBPC_HD double2 enc(double a, double b, double) { return make_double2(a, b); }
+};
+template <> struct Pair<LBPC_FP32> {
+    static LBPC_HD void dec(float2 v, float, float& a, float& b) { a = v.x; b = v.y; }
+    static LBPC_HD float2 enc(float a, float b, float) { return make_float2(a, b); }
+};
+template <> struct Pair<LBPC_FP16S> {
+    static LBPC_HD void dec(__half2 v, float s, float& a, float& b) {
+        const float2 t = __half22float2(v);
+        a = t.x + s;
+        b = t.y + s;
+    }
+    static LBPC_HD __half2 enc(float a, float b, float s) { return __floats2half2_rn(a - s, b - s); }
+};
+template <> struct Pair<LBPC_BF16S> {
+    static LBPC_HD void dec(__nv_bfloat162 v, float s, float& a, float& b) {
+        const float2 t = __bfloat1622float2(v);
+        a = t.x + s;
+        b = t.y + s;
+    }
+    static LBPC_HD __nv_bfloat162 enc(float a, float b, float s) {
+        return __floats2bfloat162_rn(a - s, b - s);
+    }
+};
+
 template <class C> LBPC_HD const Coef<C>& coef(const Args& a);
 template <> LBPC_HD const Coef<float>& coef<float>(const Args& a) { return a.cf; }
 template <> LBPC_HD const Coef<double>& coef<double>(const Args& a) { return a.cd; }
@@ -166,6 +201,15 @@ LBPC_HD C abb_source(const Args& a, const Coef<C>& k, int face, int x, int y,
 // ---------------------------------------------------------------------------------
 template <int P, int LAYOUT, bool NC>
 LBPC_HD typename Store<P>::T ldv(const typename Store<P>::T* p) {
+#if defined(__CUDA_ARCH__)
+    if constexpr (NC) return __ldg(p);
+#endif
+    return *p;
+}
+
+// Load of any type through the read-only path (device, NC) or plainly.
+template <bool NC, class X>
+LBPC_HD X ld_any(const X* p) {
 #if defined(__CUDA_ARCH__)
     if constexpr (NC) return __ldg(p);
 #endif
@@ -340,8 +384,8 @@ LBPC_HD void flow_macro(const C* f, const Coef<C>& k, C T, C fl, C& rho, C& jx,
 // D3Q19 MRT collision with forcing (Eq. 49-54) in correction form:
 // f* = f + M^-1 [ -Lambda (m - m^eq) + (I - Lambda/2) FF ], with M^-1 = M^T diag(1/|row|^2).
 template <class C>
-LBPC_HD void collide_flow(C* f, const Coef<C>& k, C T, C fl, C& ux, C& uy,
-                                             C& uz) {
+LBPC_HD void collide_flow(C* f, const Coef<C>& k, C T, C fl, C& ux, C& uy, C& uz, C& rho_o,
+                          C& jx_o, C& jy_o, C& jz_o) {
     // grouped sums: axis pairs and the xy, xz, yz diagonal quadruples
     const C a1 = f[1] + f[2], b1 = f[1] - f[2];
     const C a3 = f[3] + f[4], b3 = f[3] - f[4];
@@ -362,6 +406,10 @@ LBPC_HD void collide_flow(C* f, const Coef<C>& k, C T, C fl, C& ux, C& uy,
 
     const C rho = f[0] + sax + sdg;
     const C jx = b1 + xy_x + xz_x, jy = b3 + xy_y + yz_y, jz = b5 + xz_z + yz_z;
+    rho_o = rho;
+    jx_o = jx;
+    jy_o = jy;
+    jz_o = jz;
     // non-conserved moments (rows 1, 2, 4, 6, 8-18 of Eq. 51)
     const C m1 = C(-30) * f[0] - C(11) * sax + C(8) * sdg;
     const C m2 = C(12) * f[0] - C(4) * sax + sdg;
@@ -526,10 +574,11 @@ template <> struct KindLayout<STEP_AA_ODD> { static constexpr int value = LAYOUT
 
 // One time step of node (x, y, z): gather (stream in, with wall rules), Eq. 2 inversion,
 // flow collision, enthalpy collision, scatter, FP64 rest channel update.
-template <int P, int KIND, bool FLOW>
+template <int P, int KIND, bool FLOW, bool TAPE = false>
 LBPC_HD void step_node(const Args& a, int x, int y, int z, const typename Store<P>::T* fs,
                        typename Store<P>::T* fd, const typename Store<P>::T* gs,
-                       typename Store<P>::T* gd, double* hp) {
+                       typename Store<P>::T* gd, double* hp, double* tape_e = nullptr,
+                       typename Store<P>::C* tape_m = nullptr) {
     using S = Store<P>;
     using C = typename S::C;
     const Coef<C>& k = coef<C>(a);
@@ -552,8 +601,17 @@ LBPC_HD void step_node(const Args& a, int x, int y, int z, const typename Store<
 
     C T, fl;
     invert_excess(k, e, T, fl);
-    C ux = C(0), uy = C(0), uz = C(0);
-    if constexpr (FLOW) collide_flow(f, k, T, fl, ux, uy, uz);
+    C ux = C(0), uy = C(0), uz = C(0), rho = C(0), jx = C(0), jy = C(0), jz = C(0);
+    if constexpr (FLOW) collide_flow(f, k, T, fl, ux, uy, uz, rho, jx, jy, jz);
+    if constexpr (TAPE) {  // macroscopic tape of the pre-collision state (adjoint)
+        tape_e[n] = e;
+        if constexpr (FLOW) {
+            tape_m[n] = rho;
+            tape_m[(size_t)a.N + n] = jx;
+            tape_m[2 * (size_t)a.N + n] = jy;
+            tape_m[3 * (size_t)a.N + n] = jz;
+        }
+    }
     collide_enth(g, k, T, fl, ux, uy, uz);
     if (interior) {
         if constexpr (FLOW) scatter_f<P, KIND>(a, bi, n, fd, f);
@@ -563,6 +621,103 @@ LBPC_HD void step_node(const Args& a, int x, int y, int z, const typename Store<
         scatter_g<P, KIND>(a, b, n, x, y, z, gd, g);
     }
     hp[n] = excess_minus(e, g);
+}
+
+
+// Two nodes (x0, x0 + 1), x0 even, of a row away from every y and z face: populations
+// with e_x = 0 move as aligned pairs; e_x = +-1 ones are two scalar loads, with the
+// x-face rules applied by selects on the lanes at x = 0 / x = nx - 1; every store is a
+// pair.  Requires even nx.
+template <int P, bool FLOW>
+LBPC_HD void step_pair_pull(const Args& a, int x0, int y, int z, const typename Store<P>::T* fs,
+                            typename Store<P>::T* fd, const typename Store<P>::T* gs,
+                            typename Store<P>::T* gd, double* hp) {
+    using S = Store<P>;
+    using T = typename S::T;
+    using C = typename S::C;
+    using V = typename Vec2<T>::type;
+    using PR = Pair<P>;
+    const Coef<C>& k = coef<C>(a);
+    const size_t N = (size_t)a.N;
+    const int sy = a.nx, sz = a.nx * a.ny;
+    const int n0 = x0 + a.nx * (y + a.ny * z), n1 = n0 + 1;
+    const bool xlo = x0 == 0, xhi = x0 + 1 == a.nx - 1;
+    const bool wlo = xlo && a.wall[0], whi = xhi && a.wall[1];
+    // upwind x-neighbour of node 0 for e_x = +1 and of node 1 for e_x = -1 (with wrap)
+    const int up0 = xlo ? n0 + a.nx - 1 : n0 - 1;
+    const int up1 = xhi ? n1 - (a.nx - 1) : n1 + 1;
+    C f0[19], f1[19], g0[7], g1[7];
+    if constexpr (FLOW) {
+#define LBPC_PF(q, ex, ey, ez, op)                                                       \
+        {                                                                               \
+            const int oyz = -(ey) * sy - (ez) * sz;                                     \
+            const C sh = fshift(k, q);                                                  \
+            const T* pl = fs + (size_t)q * N;                                           \
+            if constexpr ((ex) == 0) {                                                  \
+                PR::dec(ld_any<true>(reinterpret_cast<const V*>(pl + n0 + oyz)),             \
+                        sh, f0[q], f1[q]);                                              \
+            } else if constexpr ((ex) == 1) {                                           \
+                const T* p0 = wlo ? fs + (size_t)op * N + n0 : pl + up0 + oyz;          \
+                f0[q] = S::dec(ldv<P, LAYOUT_PULL, true>(p0), sh);                      \
+                f1[q] = S::dec(ldv<P, LAYOUT_PULL, true>(pl + n0 + oyz), sh);           \
+            } else {                                                                    \
+                const T* p1 = whi ? fs + (size_t)op * N + n1 : pl + up1 + oyz;          \
+                f0[q] = S::dec(ldv<P, LAYOUT_PULL, true>(pl + n1 + oyz), sh);           \
+                f1[q] = S::dec(ldv<P, LAYOUT_PULL, true>(p1), sh);                      \
+            }                                                                           \
+        }
+        LBPC_Q19(LBPC_PF)
+#undef LBPC_PF
+    }
+#define LBPC_PG(q, ex, ey, ez, op)                                                       \
+    {                                                                                   \
+        const int oyz = -(ey) * sy - (ez) * sz;                                         \
+        const T* pl = gs + (size_t)(q - 1) * N;                                         \
+        if constexpr ((ex) == 0) {                                                      \
+            PR::dec(ld_any<true>(reinterpret_cast<const V*>(pl + n0 + oyz)),                 \
+                    k.gshift, g0[q], g1[q]);                                            \
+        } else if constexpr ((ex) == 1) {                                               \
+            const T* p0 = wlo ? gs + (size_t)(op - 1) * N + n0 : pl + up0 + oyz;        \
+            C v = S::dec(ldv<P, LAYOUT_PULL, true>(p0), k.gshift);                      \
+            if (wlo && a.wall_iso[0]) v = -v + abb_source(a, k, 0, x0, y, z);           \
+            g0[q] = v;                                                                  \
+            g1[q] = S::dec(ldv<P, LAYOUT_PULL, true>(pl + n0 + oyz), k.gshift);         \
+        } else {                                                                        \
+            const T* p1 = whi ? gs + (size_t)(op - 1) * N + n1 : pl + up1 + oyz;        \
+            C v = S::dec(ldv<P, LAYOUT_PULL, true>(p1), k.gshift);                      \
+            if (whi && a.wall_iso[1]) v = -v + abb_source(a, k, 1, x0 + 1, y, z);       \
+            g1[q] = v;                                                                  \
+            g0[q] = S::dec(ldv<P, LAYOUT_PULL, true>(pl + n1 + oyz), k.gshift);         \
+        }                                                                               \
+    }
+    LBPC_Q7(LBPC_PG)
+#undef LBPC_PG
+    const double2 ep = ld_any<true>(reinterpret_cast<const double2*>(hp + n0));
+    const double e0 = excess_plus(ep.x, g0), e1 = excess_plus(ep.y, g1);
+    C T0, fl0, T1, fl1;
+    invert_excess(k, e0, T0, fl0);
+    invert_excess(k, e1, T1, fl1);
+    C ux0 = C(0), uy0 = C(0), uz0 = C(0), ux1 = C(0), uy1 = C(0), uz1 = C(0);
+    if constexpr (FLOW) {
+        C r, jx, jy, jz;
+        collide_flow(f0, k, T0, fl0, ux0, uy0, uz0, r, jx, jy, jz);
+        collide_flow(f1, k, T1, fl1, ux1, uy1, uz1, r, jx, jy, jz);
+#define LBPC_SPF(q, ex, ey, ez, op)                                                      \
+        *reinterpret_cast<V*>(fd + (size_t)q * N + n0) = PR::enc(f0[q], f1[q], fshift(k, q));
+        LBPC_Q19(LBPC_SPF)
+#undef LBPC_SPF
+    }
+    collide_enth(g0, k, T0, fl0, ux0, uy0, uz0);
+    collide_enth(g1, k, T1, fl1, ux1, uy1, uz1);
+#define LBPC_SPG(q, ex, ey, ez, op)                                                      \
+    {                                                                                   \
+        const V v = PR::enc(g0[q], g1[q], k.gshift);                                    \
+        *reinterpret_cast<V*>(gd + (size_t)(q - 1) * N + n0) = v;                        \
+        PR::dec(v, k.gshift, g0[q], g1[q]);                                             \
+    }
+    LBPC_Q7(LBPC_SPG)
+#undef LBPC_SPG
+    *reinterpret_cast<double2*>(hp + n0) = make_double2(excess_minus(e0, g0), excess_minus(e1, g1));
 }
 
 // Macroscopic state of node n and its contributions to the diagnostics sums
@@ -715,6 +870,278 @@ LBPC_HD void dist_node(const Args& a, int x, int y, int z, const typename Store<
     }
 }
 
+// ---------------------------------------------------------------------------------
+// Adjoint (reverse mode) of one time step.  J = sum f_l(h_N); lambda is the adjoint of
+// the pre-collision populations, stored in the natural layout (f: 19 planes, g: 7 planes
+// including g_0).  The collision adjoint is evaluated from the macroscopic tape of the
+// pre-collision state (e = h - h_s, rho, j), which fixes every nonlinear factor.
+// ---------------------------------------------------------------------------------
+
+// Derivatives of the Eq. 2 inversion on the branch the forward took.
+template <class C>
+LBPC_HD void invert_excess_d(const Coef<C>& k, double e, C& T, C& fl, C& dTde, C& dfde, C& dTdL,
+                             C& dfdL) {
+    const C d = to_compute(e, C(0));
+    if (d <= C(0)) {
+        fl = C(0); T = k.Tm + d * k.Cps_inv;
+        dTde = k.Cps_inv; dfde = C(0); dTdL = C(0); dfdL = C(0);
+    } else if (d >= k.L) {
+        fl = C(1); T = k.Tm + (d - k.L) * k.Cpl_inv;
+        dTde = k.Cpl_inv; dfde = C(0); dTdL = -k.Cpl_inv; dfdL = C(0);
+    } else {
+        fl = d * k.L_inv; T = k.Tm;
+        dTde = C(0); dfde = k.L_inv; dTdL = C(0); dfdL = -fl * k.L_inv;
+    }
+}
+
+// The symmetric D3Q7 relaxation on the six moving populations: out = (I - N^-1 R N) t,
+// with t_0 = -sum t_a implied (the same operator acts on deviations in the forward).
+template <class C>
+LBPC_HD void enth_relax_op(const Coef<C>& k, const C* t, C* out) {
+    const C m1 = t[1] - t[2], m2 = t[3] - t[4], m3 = t[5] - t[6];
+    const C p12 = t[1] + t[2], p34 = t[3] + t[4], p56 = t[5] + t[6];
+    const C S = p12 + p34 + p56;
+    const C m5 = C(2) * p12 - (p34 + p56);
+    const C m6 = p34 - p56;
+    const C A = k.sig4 * S * C(1.0 / 6.0);
+    const C B = k.sig5 * m5;
+    const C D = k.sig6 * m6 * C(0.25);
+    const C hc = C(0.5) * k.sig_chi;
+    const C c12 = A + B * C(1.0 / 6.0);
+    const C c36 = A - B * C(1.0 / 12.0);
+    out[1] = t[1] - (hc * m1 + c12);
+    out[2] = t[2] - (-hc * m1 + c12);
+    out[3] = t[3] - (hc * m2 + c36 + D);
+    out[4] = t[4] - (-hc * m2 + c36 + D);
+    out[5] = t[5] - (hc * m3 + c36 - D);
+    out[6] = t[6] - (-hc * m3 + c36 - D);
+}
+
+// lf[19], lg[7]: in = adjoint of the post-collision populations, out = adjoint of the
+// pre-collision populations.  Returns the node's contribution to dJ/dL.
+template <class C, bool FLOW>
+LBPC_HD C collide_adjoint(const Coef<C>& k, double e, C rho, C jx, C jy, C jz, C* lf, C* lg) {
+    C T, fl, dTde, dfde, dTdL, dfdL;
+    invert_excess_d(k, e, T, fl, dTde, dfde, dTdL, dfdL);
+    C ux = C(0), uy = C(0), uz = C(0), usx = C(0), usy = C(0), usz = C(0), damp = C(0);
+    C Fx = C(0), Fy = C(0), Fz = C(0);
+    if constexpr (FLOW) {
+        const C Fb = k.gbeta * (T - k.Tref);
+        usx = jx; usy = jy; usz = jz + C(0.5) * Fb;
+        damp = C(-2) * (C(1) - fl);
+        Fx = damp * usx; Fy = damp * usy; Fz = Fb + damp * usz;
+        ux = fl * usx; uy = fl * usy; uz = fl * usz;
+    }
+    // enthalpy: g*_a = geq_a + K (g - geq)_a (a >= 1), g*_0 = h - sum_a g*_a
+    const C lg0 = lg[0];
+    C t[7], Kt[7];
+    for (int q = 1; q < 7; q++) t[q] = lg[q] - lg0;
+    enth_relax_op(k, t, Kt);
+    C lgeq[7];
+    for (int q = 1; q < 7; q++) lgeq[q] = t[q] - Kt[q];
+    const C Cp = fl * k.Cpl + (C(1) - fl) * k.Cps;
+    const C lcT = lgeq[1] + lgeq[2] + lgeq[3] + lgeq[4] + lgeq[5] + lgeq[6];
+    const C dx = lgeq[1] - lgeq[2], dy = lgeq[3] - lgeq[4], dz = lgeq[5] - lgeq[6];
+    const C lvT = ux * dx + uy * dy + uz * dz;
+    C lT = k.wa_cref * lcT + C(0.5) * Cp * lvT;
+    C lfl = (k.Cpl - k.Cps) * C(0.5) * T * lvT;
+    C le = lg0;
+    if constexpr (FLOW) {
+        const C vT = C(0.5) * Cp * T;
+        C lux = vT * dx, luy = vT * dy, luz = vT * dz;
+        // mu = diag(1/|row|^2) M lambda*_f (grouped sums as in the forward transform)
+        const C* L = lf;
+        const C a1 = L[1] + L[2], b1 = L[1] - L[2];
+        const C a3 = L[3] + L[4], b3 = L[3] - L[4];
+        const C a5 = L[5] + L[6], b5 = L[5] - L[6];
+        const C sxy = (L[7] + L[8]) + (L[9] + L[10]);
+        const C xy_x = (L[7] - L[8]) + (L[9] - L[10]);
+        const C xy_y = (L[7] + L[8]) - (L[9] + L[10]);
+        const C xy_p = (L[7] - L[8]) - (L[9] - L[10]);
+        const C sxz = (L[11] + L[12]) + (L[13] + L[14]);
+        const C xz_x = (L[11] - L[12]) + (L[13] - L[14]);
+        const C xz_z = (L[11] + L[12]) - (L[13] + L[14]);
+        const C xz_p = (L[11] - L[12]) - (L[13] - L[14]);
+        const C syz = (L[15] + L[16]) + (L[17] + L[18]);
+        const C yz_y = (L[15] - L[16]) + (L[17] - L[18]);
+        const C yz_z = (L[15] + L[16]) - (L[17] + L[18]);
+        const C yz_p = (L[15] - L[16]) - (L[17] - L[18]);
+        const C sax = a1 + a3 + a5, sdg = sxy + sxz + syz;
+        const C mu1 = (C(-30) * L[0] - C(11) * sax + C(8) * sdg) * C(1.0 / 2394.0);
+        const C mu2 = (C(12) * L[0] - C(4) * sax + sdg) * C(1.0 / 252.0);
+        const C mu3 = (b1 + xy_x + xz_x) * C(0.1);
+        const C mu4 = (C(-4) * b1 + xy_x + xz_x) * C(1.0 / 40.0);
+        const C mu5 = (b3 + xy_y + yz_y) * C(0.1);
+        const C mu6 = (C(-4) * b3 + xy_y + yz_y) * C(1.0 / 40.0);
+        const C mu7 = (b5 + xz_z + yz_z) * C(0.1);
+        const C mu8 = (C(-4) * b5 + xz_z + yz_z) * C(1.0 / 40.0);
+        const C mu9 = (C(2) * a1 - a3 - a5 + sxy + sxz - C(2) * syz) * C(1.0 / 36.0);
+        const C mu10 = (C(-4) * a1 + C(2) * (a3 + a5) + sxy + sxz - C(2) * syz) * C(1.0 / 72.0);
+        const C mu11 = (a3 - a5 + sxy - sxz) * C(1.0 / 12.0);
+        const C mu12 = (C(2) * (a5 - a3) + sxy - sxz) * C(1.0 / 24.0);
+        const C mu13 = xy_p * C(0.25), mu14 = yz_p * C(0.25), mu15 = xz_p * C(0.25);
+        const C mu16 = (xy_x - xz_x) * C(0.125), mu17 = (yz_y - xy_y) * C(0.125);
+        const C mu18 = (xz_z - yz_z) * C(0.125);
+        // adjoints of m^eq (rate s_k) and of FF (weight 1 - s_k/2)
+        const C q1 = k.s_e * mu1, q2 = k.s_eps * mu2, q4 = k.s_q * mu4, q6 = k.s_q * mu6,
+                q8 = k.s_q * mu8;
+        const C w9 = k.s_nu * mu9 - C(0.5) * k.s_pi * mu10;
+        const C w11 = k.s_nu * mu11 - C(0.5) * k.s_pi * mu12;
+        const C q13 = k.s_nu * mu13, q14 = k.s_nu * mu14, q15 = k.s_nu * mu15;
+        const C r1 = (C(1) - C(0.5) * k.s_e) * mu1, r2 = (C(1) - C(0.5) * k.s_eps) * mu2;
+        const C hq = C(1) - C(0.5) * k.s_q;
+        const C r4 = hq * mu4, r6 = hq * mu6, r8 = hq * mu8;
+        const C hn = C(1) - C(0.5) * k.s_nu, hpi = C(1) - C(0.5) * k.s_pi;
+        const C v9 = hn * mu9 - C(0.5) * hpi * mu10;
+        const C v11 = hn * mu11 - C(0.5) * hpi * mu12;
+        const C r13 = hn * mu13, r14 = hn * mu14, r15 = hn * mu15;
+        const C u2 = ux * ux + uy * uy + uz * uz;
+        const C c23 = C(2) / C(3);
+        const C lrho = q1 * (C(-11) + C(19) * u2) + q2 * (C(3) - C(5.5) * u2) -
+                       c23 * (q4 * ux + q6 * uy + q8 * uz) +
+                       w9 * (C(3) * ux * ux - u2) + w11 * (uy * uy - uz * uz) +
+                       q13 * ux * uy + q14 * uy * uz + q15 * ux * uz;
+        const C cu = C(38) * q1 - C(11) * q2;
+        lux += rho * (cu * ux - c23 * q4 + C(4) * w9 * ux + q13 * uy + q15 * uz);
+        luy += rho * (cu * uy - c23 * q6 - C(2) * w9 * uy + C(2) * w11 * uy + q13 * ux + q14 * uz);
+        luz += rho * (cu * uz - c23 * q8 - C(2) * w9 * uz - C(2) * w11 * uz + q14 * uy + q15 * ux);
+        const C cf = C(38) * r1 - C(11) * r2;
+        lux += cf * Fx + C(4) * v9 * Fx + r13 * Fy + r15 * Fz;
+        luy += cf * Fy - C(2) * v9 * Fy + C(2) * v11 * Fy + r13 * Fx + r14 * Fz;
+        luz += cf * Fz - C(2) * v9 * Fz - C(2) * v11 * Fz + r14 * Fy + r15 * Fx;
+        const C lFx = cf * ux - c23 * r4 + C(4) * v9 * ux + r13 * uy + r15 * uz + mu3;
+        const C lFy = cf * uy - c23 * r6 - C(2) * v9 * uy + C(2) * v11 * uy + r13 * ux + r14 * uz + mu5;
+        const C lFz = cf * uz - c23 * r8 - C(2) * v9 * uz - C(2) * v11 * uz + r14 * uy + r15 * ux + mu7;
+        // u = f_l us, F = F_b z + damp us, us = j + F_b/2 z, F_b = g beta (T - T_ref)
+        const C lusx = fl * lux + damp * lFx;
+        const C lusy = fl * luy + damp * lFy;
+        const C lusz = fl * luz + damp * lFz;
+        lfl += lux * usx + luy * usy + luz * usz + C(2) * (lFx * usx + lFy * usy + lFz * usz);
+        const C lFb = lFz + C(0.5) * lusz;
+        lT += k.gbeta * lFb;
+        // lambda_f = lambda*_f + M^T lambda_m, lambda_m = (lrho, -s mu, lj, ...)
+        const C d0 = lrho, d3 = lusx, d5 = lusy, d7 = lusz;
+        const C d1 = -k.s_e * mu1, d2 = -k.s_eps * mu2;
+        const C d4 = -k.s_q * mu4, d6 = -k.s_q * mu6, d8 = -k.s_q * mu8;
+        const C d9 = -k.s_nu * mu9, d10 = -k.s_pi * mu10, d11 = -k.s_nu * mu11, d12 = -k.s_pi * mu12;
+        const C d13 = -k.s_nu * mu13, d14 = -k.s_nu * mu14, d15 = -k.s_nu * mu15;
+        const C d16 = -k.s_t * mu16, d17 = -k.s_t * mu17, d18 = -k.s_t * mu18;
+        lf[0] += d0 - C(30) * d1 + C(12) * d2;
+        const C eax = d0 - C(11) * d1 - C(4) * d2;
+        const C ox = d3 - C(4) * d4, oy = d5 - C(4) * d6, oz = d7 - C(4) * d8;
+        const C ex1 = eax + C(2) * d9 - C(4) * d10;
+        const C ey1 = eax - d9 + C(2) * d10 + d11 - C(2) * d12;
+        const C ez1 = eax - d9 + C(2) * d10 - d11 + C(2) * d12;
+        lf[1] += ex1 + ox;
+        lf[2] += ex1 - ox;
+        lf[3] += ey1 + oy;
+        lf[4] += ey1 - oy;
+        lf[5] += ez1 + oz;
+        lf[6] += ez1 - oz;
+        const C edg = d0 + C(8) * d1 + d2;
+        const C X = d3 + d4, Y = d5 + d6, Z = d7 + d8;
+        const C exy = edg + d9 + d10 + d11 + d12;
+        lf[7] += exy + X + Y + d13 + d16 - d17;
+        lf[8] += exy - X + Y - d13 - d16 - d17;
+        lf[9] += exy + X - Y - d13 + d16 + d17;
+        lf[10] += exy - X - Y + d13 - d16 + d17;
+        const C exz = edg + d9 + d10 - d11 - d12;
+        lf[11] += exz + X + Z + d15 - d16 + d18;
+        lf[12] += exz - X + Z - d15 + d16 + d18;
+        lf[13] += exz + X - Z - d15 - d16 - d18;
+        lf[14] += exz - X - Z + d15 + d16 - d18;
+        const C eyz = edg - C(2) * d9 - C(2) * d10;
+        lf[15] += eyz + Y + Z + d14 + d17 - d18;
+        lf[16] += eyz - Y + Z - d14 - d17 - d18;
+        lf[17] += eyz + Y - Z - d14 + d17 + d18;
+        lf[18] += eyz - Y - Z + d14 - d17 + d18;
+    }
+    le += lT * dTde + lfl * dfde;
+    lg[0] = le;
+    for (int q = 1; q < 7; q++) lg[q] = Kt[q] + le;
+    return lT * dTdL + lfl * dfdL;
+}
+
+// Adjoint seed at the final state: lambda_g = d f_l / dh on every g population,
+// lambda_f = 0; returns d f_l / dL and writes f_l (for J).
+template <int P, bool FLOW>
+LBPC_HD typename Store<P>::C adj_seed_node(const Args& a, int x, int y, int z,
+                                           const typename Store<P>::T* gs, const double* hp,
+                                           typename Store<P>::C* lam, double& fl_out) {
+    using C = typename Store<P>::C;
+    const Coef<C>& k = coef<C>(a);
+    const int n = x + a.nx * (y + a.ny * z);
+    const Nb b = make_nb(a, x, y, z);
+    C g[7];
+    gather_g<P, LAYOUT_PULL, true>(a, b, n, x, y, z, gs, g);
+    const double e = excess_plus(hp[n], g);
+    C T, fl, dTde, dfde, dTdL, dfdL;
+    invert_excess_d(k, e, T, fl, dTde, dfde, dTdL, dfdL);
+    const size_t N = (size_t)a.N;
+    const int nf = FLOW ? 19 : 0;
+    for (int q = 0; q < nf; q++) lam[(size_t)q * N + n] = C(0);
+    for (int q = 0; q < 7; q++) lam[(size_t)(nf + q) * N + n] = dfde;
+    fl_out = (double)fl;
+    return dfdL;
+}
+
+// One reverse step of node y: transposed stream (gather of lambda_{n+1} from the
+// downwind neighbours, with the transposed wall rules) then transposed collision with
+// the tape of step n.  Accumulates dJ/dT_w of face `wface` and returns the dJ/dL part.
+template <int P, bool FLOW, class NB>
+LBPC_HD typename Store<P>::C adj_reverse_node(const Args& a, const NB& b, int x, int y, int z,
+                                              const typename Store<P>::C* lin,
+                                              typename Store<P>::C* lout, const double* tape_e,
+                                              const typename Store<P>::C* tape_m, int wface,
+                                              double* gtw) {
+    using C = typename Store<P>::C;
+    const Coef<C>& k = coef<C>(a);
+    const int n = x + a.nx * (y + a.ny * z);
+    const size_t N = (size_t)a.N;
+    constexpr int nf = FLOW ? 19 : 0;
+    C lf[19], lg[7];
+    if constexpr (FLOW) {
+#define LBPC_AF(q, ex, ey, ez, op)                                                       \
+        {                                                                               \
+            const bool w = b.template wall<-(ex), -(ey), -(ez)>();                      \
+            lf[q] = w ? lin[(size_t)op * N + n]                                         \
+                      : lin[(size_t)q * N + n + b.template off<-(ex), -(ey), -(ez)>()];  \
+        }
+        LBPC_Q19(LBPC_AF)
+#undef LBPC_AF
+    }
+    lg[0] = lin[(size_t)nf * N + n];
+#define LBPC_AG(q, ex, ey, ez, op)                                                       \
+    {                                                                                   \
+        const bool w = b.template wall<-(ex), -(ey), -(ez)>();                          \
+        if (w) {                                                                        \
+            const C la = lin[(size_t)(nf + op) * N + n];                                \
+            if (a.wall_iso[op - 1]) {                                                   \
+                lg[q] = -la;                                                            \
+                if (op - 1 == wface)                                                    \
+                    gtw[face_index(a, op - 1, x, y, z)] += (double)k.wT_cref * (double)la; \
+            } else {                                                                    \
+                lg[q] = la;                                                             \
+            }                                                                           \
+        } else {                                                                        \
+            lg[q] = lin[(size_t)(nf + q) * N + n + b.template off<-(ex), -(ey), -(ez)>()]; \
+        }                                                                               \
+    }
+    LBPC_Q7(LBPC_AG)
+#undef LBPC_AG
+    C rho = C(0), jx = C(0), jy = C(0), jz = C(0);
+    if constexpr (FLOW) {
+        rho = tape_m[n];
+        jx = tape_m[N + n];
+        jy = tape_m[2 * N + n];
+        jz = tape_m[3 * N + n];
+    }
+    const C dL = collide_adjoint<C, FLOW>(k, tape_e[n], rho, jx, jy, jz, lf, lg);
+    for (int q = 0; q < nf; q++) lout[(size_t)q * N + n] = lf[q];
+    for (int q = 0; q < 7; q++) lout[(size_t)(nf + q) * N + n] = lg[q];
+    return dL;
+}
+
 #if defined(__CUDACC__)
 // ---------------------------------------------------------------------------------
 // Kernels: one thread per node on a (x-block, y-block, z) grid.
@@ -731,6 +1158,29 @@ k_step(const __grid_constant__ Args a, const typename Store<P>::T* fs, typename 
        const typename Store<P>::T* gs, typename Store<P>::T* gd, double* __restrict__ hp) {
     LBPC_NODE_XYZ
     step_node<P, KIND, FLOW>(a, x, y, z, fs, fd, gs, gd, hp);
+}
+
+
+// Pull step, two nodes per thread along x (even nx).  Warps whose rows all lie away
+// from the y and z faces take the paired path; others run the per-node path twice.
+template <int P, bool FLOW>
+__global__ void __launch_bounds__(STEP_THREADS)
+k_step_pull_x2(const __grid_constant__ Args a, const typename Store<P>::T* fs,
+               typename Store<P>::T* fd, const typename Store<P>::T* gs, typename Store<P>::T* gd,
+               double* __restrict__ hp) {
+    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    const bool valid = x0 < a.nx && y < a.ny;
+    const bool inner = !valid || (y > 0 && y < a.ny - 1 && z > 0 && z < a.nz - 1);
+    const bool paired = __all_sync(0xffffffffu, inner);
+    if (!valid) return;
+    if (paired) {
+        step_pair_pull<P, FLOW>(a, x0, y, z, fs, fd, gs, gd, hp);
+    } else {
+        step_node<P, STEP_PULL, FLOW>(a, x0, y, z, fs, fd, gs, gd, hp);
+        step_node<P, STEP_PULL, FLOW>(a, x0 + 1, y, z, fs, fd, gs, gd, hp);
+    }
 }
 
 template <class T>
@@ -792,13 +1242,79 @@ k_dist(const __grid_constant__ Args a, const typename Store<P>::T* __restrict__ 
     dist_node<P, LAYOUT, FLOW>(a, x, y, z, fs, gs, hp, Qf, Qg);
 }
 
+
+// ---- adjoint kernels ----
+template <int P, bool FLOW>
+__global__ void __launch_bounds__(STEP_THREADS)
+k_step_tape(const __grid_constant__ Args a, const typename Store<P>::T* fs, typename Store<P>::T* fd,
+            const typename Store<P>::T* gs, typename Store<P>::T* gd, double* __restrict__ hp,
+            double* __restrict__ tape_e, typename Store<P>::C* __restrict__ tape_m) {
+    LBPC_NODE_XYZ
+    step_node<P, STEP_PULL, FLOW, true>(a, x, y, z, fs, fd, gs, gd, hp, tape_e, tape_m);
+}
+
+// Sum of v over the block (STEP_THREADS threads), valid in thread 0.
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double sh[STEP_THREADS / 32];
+    v = warp_sum(v);
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    if ((tid & 31) == 0) sh[tid >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (tid == 0)
+        for (int w = 0; w < STEP_THREADS / 32; w++) s += sh[w];
+    return s;
+}
+
+__device__ __forceinline__ int block_linear() {
+    return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+}
+
+template <int P, bool FLOW>
+__global__ void __launch_bounds__(STEP_THREADS)
+k_adj_seed(const __grid_constant__ Args a, const typename Store<P>::T* __restrict__ gs,
+           const double* __restrict__ hp, typename Store<P>::C* __restrict__ lam,
+           double* __restrict__ Lpart, double* __restrict__ Jpart) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    double dL = 0.0, fl = 0.0;
+    if (x < a.nx && y < a.ny) dL = (double)adj_seed_node<P, FLOW>(a, x, y, z, gs, hp, lam, fl);
+    const double sL = block_sum(dL);
+    __syncthreads();
+    const double sJ = block_sum(fl);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        Lpart[block_linear()] = sL;
+        Jpart[block_linear()] = sJ;
+    }
+}
+
+template <int P, bool FLOW>
+__global__ void __launch_bounds__(STEP_THREADS)
+k_adj_reverse(const __grid_constant__ Args a, const typename Store<P>::C* __restrict__ lin,
+              typename Store<P>::C* __restrict__ lout, const double* __restrict__ tape_e,
+              const typename Store<P>::C* __restrict__ tape_m, int wface, double* gtw,
+              double* __restrict__ Lpart) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    double dL = 0.0;
+    if (x < a.nx && y < a.ny) {
+        if (is_interior(a, x, y, z))
+            dL = (double)adj_reverse_node<P, FLOW>(a, NbInterior{a.nx, a.nx * a.ny}, x, y, z, lin,
+                                                   lout, tape_e, tape_m, wface, gtw);
+        else
+            dL = (double)adj_reverse_node<P, FLOW>(a, make_nb(a, x, y, z), x, y, z, lin, lout,
+                                                   tape_e, tape_m, wface, gtw);
+    }
+    const double s = block_sum(dL);
+    if (threadIdx.x == 0 && threadIdx.y == 0) Lpart[block_linear()] += s;
+}
+
 // ---------------------------------------------------------------------------------
 // Host launchers.
 // ---------------------------------------------------------------------------------
-inline dim3 node_block(const Args& a) {
-    const int bx = a.nx >= 128 ? 128 : (a.nx > 32 ? 64 : 32);
-    return dim3(bx, STEP_THREADS / bx, 1);
-}
+inline dim3 node_block(const Args& a) { return node_block_dims(a.nx); }
 inline dim3 node_grid(const Args& a, dim3 blk) {
     return dim3((a.nx + blk.x - 1) / blk.x, (a.ny + blk.y - 1) / blk.y, a.nz);
 }
@@ -810,6 +1326,14 @@ struct Impl {
     template <int KIND, bool FLOW>
     static void step_k(const Args& a, const void* fs, void* fd, const void* gs, void* gd,
                        double* hp, cudaStream_t s) {
+        if (KIND == STEP_PULL && P != LBPC_FP64 && a.nx % 2 == 0) {
+            const int pairs = a.nx / 2;
+            const dim3 blk = node_block_dims(pairs);
+            const dim3 grd((pairs + blk.x - 1) / blk.x, (a.ny + blk.y - 1) / blk.y, a.nz);
+            k_step_pull_x2<P, FLOW><<<grd, blk, 0, s>>>(a, (const T*)fs, (T*)fd, (const T*)gs,
+                                                        (T*)gd, hp);
+            return;
+        }
         const dim3 blk = node_block(a), grd = node_grid(a, blk);
         k_step<P, KIND, FLOW><<<grd, blk, 0, s>>>(a, (const T*)fs, (T*)fd, (const T*)gs, (T*)gd, hp);
     }
@@ -872,8 +1396,40 @@ struct Impl {
         else dist_k<LAYOUT_AA_SWAPPED>(a, f, g, hp, Qf, Qg, s);
     }
 
+    static void step_tape(const Args& a, const void* fs, void* fd, const void* gs, void* gd,
+                          double* hp, double* tape_e, void* tape_m, cudaStream_t s) {
+        const dim3 blk = node_block(a), grd = node_grid(a, blk);
+        using C = typename Store<P>::C;
+        if (a.flow)
+            k_step_tape<P, true><<<grd, blk, 0, s>>>(a, (const T*)fs, (T*)fd, (const T*)gs, (T*)gd,
+                                                     hp, tape_e, (C*)tape_m);
+        else
+            k_step_tape<P, false><<<grd, blk, 0, s>>>(a, (const T*)fs, (T*)fd, (const T*)gs, (T*)gd,
+                                                      hp, tape_e, (C*)tape_m);
+    }
+    static void adj_seed(const Args& a, const void* gs, const double* hp, void* lam,
+                         double* Lpart, double* Jpart, cudaStream_t s) {
+        const dim3 blk = node_block(a), grd = node_grid(a, blk);
+        using C = typename Store<P>::C;
+        if (a.flow) k_adj_seed<P, true><<<grd, blk, 0, s>>>(a, (const T*)gs, hp, (C*)lam, Lpart, Jpart);
+        else k_adj_seed<P, false><<<grd, blk, 0, s>>>(a, (const T*)gs, hp, (C*)lam, Lpart, Jpart);
+    }
+    static void adj_reverse(const Args& a, const void* lin, void* lout, const double* tape_e,
+                            const void* tape_m, int wface, double* gtw, double* Lpart,
+                            cudaStream_t s) {
+        const dim3 blk = node_block(a), grd = node_grid(a, blk);
+        using C = typename Store<P>::C;
+        if (a.flow)
+            k_adj_reverse<P, true><<<grd, blk, 0, s>>>(a, (const C*)lin, (C*)lout, tape_e,
+                                                       (const C*)tape_m, wface, gtw, Lpart);
+        else
+            k_adj_reverse<P, false><<<grd, blk, 0, s>>>(a, (const C*)lin, (C*)lout, tape_e,
+                                                        (const C*)tape_m, wface, gtw, Lpart);
+    }
+
     static const Launchers& table() {
-        static const Launchers L = {&step, &macro, &init, &dist, sizeof(T)};
+        static const Launchers L = {&step, &macro, &init, &dist, &step_tape, &adj_seed,
+                                    &adj_reverse, sizeof(T), sizeof(typename Store<P>::C)};
         return L;
     }
 };

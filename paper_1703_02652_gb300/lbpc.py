@@ -155,6 +155,42 @@ class LBPC:
                                                        _dptr(g)))
         self.stream.synchronize()
 
+    # -- adjoint ---------------------------------------------------------------------
+    def _face_area(self, face):
+        return [self.ny * self.nz] * 2 + [self.nx * self.nz] * 2 + [self.nx * self.ny] * 2
+
+    def adjoint_forward(self, nsteps: int, ckpt_every: int) -> float:
+        """Advance nsteps with checkpoints; returns J = sum f_l at the end.  The adjoint
+        workspace (a torch uint8 tensor) is kept on the object for adjoint_backward."""
+        n = int(B.lib().lbpc_adjoint_workspace_bytes(self._h, int(nsteps), int(ckpt_every)))
+        if n == 0:
+            raise ValueError("invalid nsteps / ckpt_every")
+        ws = getattr(self, "_adj_ws", None)
+        if ws is None or ws.numel() < n:
+            self._adj_ws = None
+            self._adj_ws = torch.empty(n, dtype=torch.uint8, device=self.device)
+        J = C.c_double()
+        self._check(B.lib().lbpc_adjoint_forward(self._h, int(nsteps), int(ckpt_every),
+                                                 C.c_void_p(self._adj_ws.data_ptr()),
+                                                 self._adj_ws.numel(), C.byref(J)))
+        return J.value
+
+    def adjoint_backward(self, face: int = 0):
+        """Gradients of the last adjoint_forward's J: (dJ/dT_w of `face`, dJ/dSt)."""
+        g = np.zeros(self._face_area(face)[face])
+        dSt = C.c_double()
+        self._check(B.lib().lbpc_adjoint_backward(self._h, int(face), _hptr(g), C.byref(dSt)))
+        return g, dSt.value
+
+    def adjoint(self, nsteps: int, ckpt_every: int, face: int = 0):
+        """(J, dJ/dT_w of `face`, dJ/dSt) for nsteps steps from the current state."""
+        J = self.adjoint_forward(nsteps, ckpt_every)
+        g, dSt = self.adjoint_backward(face)
+        return J, g, dSt
+
+    def release_adjoint_workspace(self):
+        self._adj_ws = None
+
     # -- checkpoint ------------------------------------------------------------------
     def save(self) -> bytes:
         n = int(B.lib().lbpc_state_bytes(self._h))

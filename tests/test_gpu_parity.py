@@ -127,8 +127,9 @@ TOL = {inp.FP64: 1e-13, inp.FP32: 5e-6, inp.FP16: 2.5e-4, inp.BF16: 2e-3}
 @pytest.mark.parametrize("precision", [inp.FP64, inp.FP32, inp.FP16, inp.BF16])
 @pytest.mark.parametrize("streaming", [inp.PULL, inp.AA])
 @pytest.mark.parametrize("flow_model", [inp.FLOW_MRT, inp.FLOW_SRT, inp.FLOW_NONE])
-def test_one_step_from_random_state(precision, streaming, flow_model):
-    shape = (19, 6, 5)
+@pytest.mark.parametrize("nx", [19, 20])  # odd: one node per thread; even: node pairs
+def test_one_step_from_random_state(precision, streaming, flow_model, nx):
+    shape = (nx, 6, 5)
     p = inp.Params(flow_model=flow_model, precision=precision, streaming=streaming,
                    Ra=5e4, Pr=0.5, St=0.7, tau_g=0.0 if flow_model else 0.9,
                    bc=[inp.ISOTHERMAL, inp.ISOTHERMAL, inp.PERIODIC, inp.PERIODIC,
