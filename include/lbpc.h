@@ -214,6 +214,26 @@ lbpc_status lbpc_adjoint_backward(lbpc_handle *h, int face, double *dJ_dTw_host,
 lbpc_status lbpc_adjoint(lbpc_handle *h, int nsteps, int ckpt_every, void *dev_ws, size_t ws_bytes,
                          int face, double *J_host, double *dJ_dTw_host, double *dJ_dSt_host);
 
+/*
+ * lbpc_get_scalars_noalloc: the LBPC_S_* diagnostics of the current state, like
+ * lbpc_get_scalars, for callers that cannot allocate device memory at that point (a
+ * device whose free memory is owned by a pool, code that must not call cudaMalloc or
+ * cudaFree because they may synchronise the device, a memory budget fixed before the
+ * run).  The paper has no counterpart; this is an interface convenience.
+ *
+ * out_dev: device buffer of LBPC_S_COUNT doubles, written in stream order on the
+ * handle's stream; the call does not wait for the result.  The block partial sums live
+ * in a static device array of about 152 KB that the library holds on every device that
+ * loads it, until the process exits; no memory is allocated.  The first call on a device
+ * looks the array's address up (cudaGetSymbolAddress) and caches it, so make that first
+ * call before any stream capture.  All calls share the array: calls whose executions
+ * overlap on the GPU (other streams, other handles, other threads) race on it and must
+ * be serialised by the caller.  LBPC_ERR_PARAM if nx > LBPC_NOALLOC_MAX_NX or out_dev is
+ * NULL.
+ */
+#define LBPC_NOALLOC_MAX_NX 4096
+lbpc_status lbpc_get_scalars_noalloc(lbpc_handle *h, double *out_dev);
+
 long long lbpc_step_count(const lbpc_handle *h);
 /* Number of kernels this handle has launched since it was created. */
 long long lbpc_launch_count(const lbpc_handle *h);

@@ -28,7 +28,7 @@ EXPORTS = ["lbpc_params_size", "lbpc_abi_version", "lbpc_workspace_bytes", "lbpc
            "lbpc_get_fields_dev", "lbpc_get_scalars", "lbpc_get_history",
            "lbpc_get_distributions_dev", "lbpc_set_distributions_dev", "lbpc_get_lattice",
            "lbpc_lattice_constants", "lbpc_adjoint_workspace_bytes", "lbpc_adjoint_forward",
-           "lbpc_adjoint_backward", "lbpc_adjoint",
+           "lbpc_adjoint_backward", "lbpc_adjoint", "lbpc_get_scalars_noalloc",
            "lbpc_state_bytes", "lbpc_save", "lbpc_load", "lbpc_step_count", "lbpc_launch_count",
            "lbpc_last_error",
            "lbpc_destroy"]
@@ -84,6 +84,7 @@ def lib(build: bool = True):
     L.lbpc_adjoint_forward.argtypes = [vp, C.c_int, C.c_int, vp, sz, d]
     L.lbpc_adjoint_backward.argtypes = [vp, C.c_int, d, d]
     L.lbpc_adjoint.argtypes = [vp, C.c_int, C.c_int, vp, sz, C.c_int, d, d, d]
+    L.lbpc_get_scalars_noalloc.argtypes = [vp, vp]
     L.lbpc_state_bytes.restype = sz
     L.lbpc_state_bytes.argtypes = [vp]
     L.lbpc_save.argtypes = [vp, vp, sz]

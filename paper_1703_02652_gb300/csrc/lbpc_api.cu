@@ -787,3 +787,44 @@ lbpc_status lbpc_adjoint(lbpc_handle* h, int nsteps, int ckpt_every, void* dev_w
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------
+// Read-only view of a handle for lbpc_noalloc.cu.
+// ---------------------------------------------------------------------------------
+namespace lbpc_noalloc_access {
+struct View {
+    const Launchers* L;
+    const Args* args;
+    Layout layout;
+    const void* f;
+    const void* g;
+    const double* hp;
+    int nx, ny, nz, device, flow, iso0;
+    double nu_scale, fd_scale, step;
+    cudaStream_t stream;
+};
+
+lbpc_status view(lbpc_handle* h, View* v) {
+    lbpc_status s = set_device(h);
+    if (s != LBPC_OK) return s;
+    v->L = h->L;
+    v->args = &h->args;
+    v->layout = current_layout(h);
+    v->f = cur_f(h);
+    v->g = cur_g(h);
+    v->hp = h->hp;
+    v->nx = h->nx;
+    v->ny = h->ny;
+    v->nz = h->nz;
+    v->device = h->device;
+    v->flow = h->p.flow_model != LBPC_FLOW_NONE;
+    v->iso0 = h->p.bc[0] == LBPC_ISOTHERMAL;
+    v->nu_scale = h->d.H / (h->d.chi * h->p.Cp_ref * h->d.dT);
+    v->fd_scale = h->d.H / h->d.dT;
+    v->step = (double)h->step;
+    v->stream = h->stream;
+    return LBPC_OK;
+}
+
+void set_error(lbpc_handle* h, const char* msg) { h->err = msg; }
+}  // namespace lbpc_noalloc_access
