@@ -31,7 +31,8 @@ sys.path.insert(0, ROOT)
 import lbpc_inputs as inp  # noqa: E402
 
 METRIC = "coupled flow+enthalpy MLUPS, % of HBM roofline; adjoint/forward time ratio"
-BYTES_PER_LUP = {inp.FP64: 416, inp.FP32: 216, inp.FP16: 116, inp.BF16: 116}
+BYTES_PER_LUP = {inp.FP64: 416, inp.FP32: 216, inp.FP16: 116, inp.BF16: 116, inp.FP16_G32: 140,
+                 inp.BF16_G32: 140}
 SAMPLE_SHAPE = (256, 32, 32)  # oracle sample: a slab of the same cavity (same lattice constants)
 
 
@@ -130,6 +131,23 @@ def _dist():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """The largest value of x over all ranks (the slowest replica sets the job time)."""
+    if dist is None:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(world: int, nodes: int, steps: int, seconds: float) -> float:
+    """Whole-job throughput of `world` independent replicas of `nodes` lattice nodes each,
+    all advanced `steps` steps within `seconds` (max over ranks)."""
+    return world * nodes * steps / seconds / 1e6
 
 
 def cpu_baseline(seconds=15.0, min_steps=2):
@@ -236,7 +254,8 @@ def run_ours(args):
     if args.lattice != 256:  # smaller cavity of the same physics, for profiling
         w = inp.cavity_melting(n=args.lattice, Ra=1e6, Pr=0.02, St=1.0, precision=inp.FP32,
                                steps=w.steps, report_every=w.params.report_every)
-    precision = {"f32": inp.FP32, "f16": inp.FP16, "bf16": inp.BF16, "f64": inp.FP64}[args.precision]
+    precision = {"f32": inp.FP32, "f16": inp.FP16, "bf16": inp.BF16, "f64": inp.FP64,
+                 "f16g32": inp.FP16_G32, "bf16g32": inp.BF16_G32}[args.precision]
     streaming = inp.AA if args.streaming == "aa" else inp.PULL
     p = w.params.replace(precision=precision, streaming=streaming)
     h0 = inp.h0_field(w)
@@ -265,15 +284,11 @@ def run_ours(args):
     barrier()
     clocks = sampler.stop() if sampler else None
     launches = g.launch_count - launches0
-    ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, device="cuda")
     s = g.scalars()
     assert s["nan"] == 0, "diverged during the timed region"
-    value = world * w.nodes * args.steps / (ms * 1e-3) / 1e6
-    per_rank = w.nodes * args.steps / (ms * 1e-3) / 1e6
+    value = job_mlups(world, w.nodes, args.steps, ms * 1e-3)
+    per_rank = job_mlups(1, w.nodes, args.steps, ms * 1e-3)
     del g
     torch.cuda.empty_cache()
 
@@ -287,11 +302,7 @@ def run_ours(args):
     out = ge.fields_host(mask=1 | 2)  # T and f_l to host
     sc = ge.scalars()
     torch.cuda.synchronize()
-    te = time.perf_counter() - t0
-    te_t = torch.tensor([te], device="cuda", dtype=torch.float64)
-    if dist is not None:
-        dist.all_reduce(te_t, op=dist.ReduceOp.MAX)
-    te = float(te_t.item())
+    te = max_over_ranks(time.perf_counter() - t0, dist, device="cuda")
     assert sc["nan"] == 0 and np.isfinite(out["T"]).all()
     del ge
     torch.cuda.empty_cache()
@@ -310,7 +321,9 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": {inp.FP32: "f32", inp.FP16: "f32 (f16-shifted storage)",
-                  inp.BF16: "f32 (bf16-shifted storage)", inp.FP64: "f64"}[precision],
+                  inp.BF16: "f32 (bf16-shifted storage)", inp.FP64: "f64",
+                  inp.FP16_G32: "f32 (f16-shifted f, f32 g storage)",
+                  inp.BF16_G32: "f32 (bf16-shifted f, f32 g storage)"}[precision],
         "data": "synthetic",
         "config": {"workload": w.name + " D3Q19-MRT + D3Q7-MRT", "lattice": list(w.shape),
                    "precision": inp.PRECISION_NAMES[precision],
@@ -325,7 +338,7 @@ def run_ours(args):
                      "traffic_per_lup": tr},
         "gpu_launches": launches,
         "clocks": clocks,
-        "e2e": {"value": world * w.nodes * args.steps / te / 1e6, "unit": "MLUPS",
+        "e2e": {"value": job_mlups(world, w.nodes, args.steps, te), "unit": "MLUPS",
                 "h2d_bytes_per_step": 8 * w.nodes / args.steps,
                 "d2h_bytes_per_step": (16 * w.nodes + 8 * 9) / args.steps,
                 "what": "create + initial h from pinned host + K steps + T, f_l and scalars "
@@ -347,7 +360,8 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="f32", choices=["f32", "f16", "bf16", "f64"])
+    ap.add_argument("--precision", default="f32",
+                    choices=["f32", "f16", "bf16", "f64", "f16g32", "bf16g32"])
     ap.add_argument("--streaming", default="pull", choices=["pull", "aa"])
     ap.add_argument("--lattice", type=int, default=256, help="cavity edge (profiling only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -48,8 +48,12 @@ enum { LBPC_PERIODIC = 0, LBPC_ISOTHERMAL = 1, LBPC_ADIABATIC = 2 };
 enum { LBPC_FLOW_NONE = 0, LBPC_FLOW_MRT = 1, LBPC_FLOW_SRT = 2 };
 enum { LBPC_ENTH_MRT = 1, LBPC_ENTH_SRT = 2 };
 /* storage precision of the populations; collision runs in FP64 for LBPC_FP64 and in
- * FP32 registers otherwise; h', the H -> (T, f_l) inversion and reductions are FP64. */
-enum { LBPC_FP64 = 0, LBPC_FP32 = 1, LBPC_FP16S = 2, LBPC_BF16S = 3 };
+ * FP32 registers otherwise; h', the H -> (T, f_l) inversion and reductions are FP64.
+ * FP16S / BF16S store f - w_a and g_a - (omega_T/2) Cp_ref Tref in 16 bits (116 B per
+ * node update); the _G32 modes store f that way and g in FP32 (140 B), which keeps the
+ * enthalpy populations and the wall fluxes they carry at FP32 resolution. */
+enum { LBPC_FP64 = 0, LBPC_FP32 = 1, LBPC_FP16S = 2, LBPC_BF16S = 3, LBPC_FP16S_G32 = 4,
+       LBPC_BF16S_G32 = 5 };
 enum { LBPC_PULL = 0, LBPC_AA = 1 };
 
 /*

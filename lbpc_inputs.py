@@ -22,9 +22,10 @@ import numpy as np
 PERIODIC, ISOTHERMAL, ADIABATIC = 0, 1, 2
 FLOW_NONE, FLOW_MRT, FLOW_SRT = 0, 1, 2
 ENTH_MRT, ENTH_SRT = 1, 2
-FP64, FP32, FP16, BF16 = 0, 1, 2, 3
+FP64, FP32, FP16, BF16, FP16_G32, BF16_G32 = 0, 1, 2, 3, 4, 5
 PULL, AA = 0, 1
-PRECISION_NAMES = {FP64: "f64", FP32: "f32", FP16: "f16s", BF16: "bf16s"}
+PRECISION_NAMES = {FP64: "f64", FP32: "f32", FP16: "f16s", BF16: "bf16s", FP16_G32: "f16s-g32",
+                   BF16_G32: "bf16s-g32"}
 
 
 @dataclass

@@ -30,8 +30,12 @@ constexpr uint32_t kStateMagic = 0x4c425043u;  // "LBPC"
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
-size_t store_bytes(int precision) {
+// bytes of one stored f / g value of a storage mode
+size_t f_store_bytes(int precision) {
     return precision == LBPC_FP64 ? 8 : (precision == LBPC_FP32 ? 4 : 2);
+}
+size_t g_store_bytes(int precision) {
+    return precision == LBPC_FP64 ? 8 : (precision == LBPC_FP16S || precision == LBPC_BF16S ? 2 : 4);
 }
 
 long face_area(int nx, int ny, int nz, int face) {
@@ -40,17 +44,18 @@ long face_area(int nx, int ny, int nz, int face) {
 
 WsLayout ws_layout(int nx, int ny, int nz, const lbpc_params* p) {
     WsLayout w{};
-    const size_t N = (size_t)nx * ny * nz, S = store_bytes(p->precision);
+    const size_t N = (size_t)nx * ny * nz, Sf = f_store_bytes(p->precision),
+                 Sg = g_store_bytes(p->precision);
     const bool flow = p->flow_model != LBPC_FLOW_NONE;
     const int nlat = p->streaming == LBPC_PULL ? 2 : 1;
     size_t off = 0;
     for (int i = 0; i < 2; i++) {
         w.f[i] = off;
-        if (flow && i < nlat) off = align_up(off + 19 * N * S);
+        if (flow && i < nlat) off = align_up(off + 19 * N * Sf);
     }
     for (int i = 0; i < 2; i++) {
         w.g[i] = off;
-        if (i < nlat) off = align_up(off + 6 * N * S);
+        if (i < nlat) off = align_up(off + 6 * N * Sg);
     }
     w.hp = off; off = align_up(off + 8 * N);
     for (int f = 0; f < 6; f++) { w.tw[f] = off; off = align_up(off + 8 * face_area(nx, ny, nz, f)); }
@@ -289,7 +294,9 @@ lbpc_status lbpc_create(int nx, int ny, int nz, const lbpc_params* p, void* dev_
         case LBPC_FP64: h->L = &launchers_f64(); break;
         case LBPC_FP32: h->L = &launchers_f32(); break;
         case LBPC_FP16S: h->L = &launchers_f16(); break;
-        default: h->L = &launchers_bf16(); break;
+        case LBPC_BF16S: h->L = &launchers_bf16(); break;
+        case LBPC_FP16S_G32: h->L = &launchers_f16g32(); break;
+        default: h->L = &launchers_bf16g32(); break;
     }
     h->ws = (char*)dev_ws;
     h->ws_bytes = ws_bytes;
@@ -522,9 +529,9 @@ struct StateHeader {
 };
 
 size_t state_pop_bytes(const lbpc_handle* h, size_t* fb, size_t* gb) {
-    const size_t S = h->L->store_bytes, N = (size_t)h->N;
-    *fb = h->p.flow_model != LBPC_FLOW_NONE ? 19 * N * S : 0;
-    *gb = 6 * N * S;
+    const size_t N = (size_t)h->N;
+    *fb = h->p.flow_model != LBPC_FLOW_NONE ? 19 * N * h->L->f_bytes : 0;
+    *gb = 6 * N * h->L->g_bytes;
     size_t tw = 0;
     for (int f = 0; f < 6; f++) tw += 8 * face_area(h->nx, h->ny, h->nz, f);
     return sizeof(StateHeader) + *fb + *gb + 8 * N + tw;
@@ -619,12 +626,13 @@ struct AdjLayout {
 
 AdjLayout adj_layout(const lbpc_handle* h, int nsteps, int k) {
     AdjLayout L{};
-    const size_t N = (size_t)h->N, S = h->L->store_bytes, Cb = h->L->compute_bytes;
+    const size_t N = (size_t)h->N, Sf = h->L->f_bytes, Sg = h->L->g_bytes,
+                 Cb = h->L->compute_bytes;
     const bool flow = h->p.flow_model != LBPC_FLOW_NONE;
     L.nseg = (nsteps + k - 1) / k;
     L.off_f = 0;
-    L.off_g = align_up(flow ? 19 * N * S : 0);
-    L.off_hp = L.off_g + align_up(6 * N * S);
+    L.off_g = align_up(flow ? 19 * N * Sf : 0);
+    L.off_hp = L.off_g + align_up(6 * N * Sg);
     L.ckpt_bytes = L.off_hp + align_up(8 * N);
     size_t off = 0;
     L.ckpt = off; off += (size_t)(L.nseg + 1) * L.ckpt_bytes;
@@ -646,21 +654,21 @@ AdjLayout adj_layout(const lbpc_handle* h, int nsteps, int k) {
 
 lbpc_status save_state(lbpc_handle* h, char* dst) {
     auto& A = h->adj;
-    const size_t N = (size_t)h->N, S = h->L->store_bytes;
+    const size_t N = (size_t)h->N, Sf = h->L->f_bytes, Sg = h->L->g_bytes;
     if (h->p.flow_model != LBPC_FLOW_NONE)
-        LBPC_CK(h, cudaMemcpyAsync(dst + A.off_f, h->f[h->cur], 19 * N * S, cudaMemcpyDeviceToDevice, h->stream));
-    LBPC_CK(h, cudaMemcpyAsync(dst + A.off_g, h->g[h->cur], 6 * N * S, cudaMemcpyDeviceToDevice, h->stream));
+        LBPC_CK(h, cudaMemcpyAsync(dst + A.off_f, h->f[h->cur], 19 * N * Sf, cudaMemcpyDeviceToDevice, h->stream));
+    LBPC_CK(h, cudaMemcpyAsync(dst + A.off_g, h->g[h->cur], 6 * N * Sg, cudaMemcpyDeviceToDevice, h->stream));
     LBPC_CK(h, cudaMemcpyAsync(dst + A.off_hp, h->hp, 8 * N, cudaMemcpyDeviceToDevice, h->stream));
     return LBPC_OK;
 }
 
 lbpc_status restore_state(lbpc_handle* h, const char* src) {
     auto& A = h->adj;
-    const size_t N = (size_t)h->N, S = h->L->store_bytes;
+    const size_t N = (size_t)h->N, Sf = h->L->f_bytes, Sg = h->L->g_bytes;
     h->cur = 0;
     if (h->p.flow_model != LBPC_FLOW_NONE)
-        LBPC_CK(h, cudaMemcpyAsync(h->f[0], src + A.off_f, 19 * N * S, cudaMemcpyDeviceToDevice, h->stream));
-    LBPC_CK(h, cudaMemcpyAsync(h->g[0], src + A.off_g, 6 * N * S, cudaMemcpyDeviceToDevice, h->stream));
+        LBPC_CK(h, cudaMemcpyAsync(h->f[0], src + A.off_f, 19 * N * Sf, cudaMemcpyDeviceToDevice, h->stream));
+    LBPC_CK(h, cudaMemcpyAsync(h->g[0], src + A.off_g, 6 * N * Sg, cudaMemcpyDeviceToDevice, h->stream));
     LBPC_CK(h, cudaMemcpyAsync(h->hp, src + A.off_hp, 8 * N, cudaMemcpyDeviceToDevice, h->stream));
     return LBPC_OK;
 }

@@ -22,7 +22,7 @@ inline bool validate_and_map(int nx, int ny, int nz, const lbpc_params* p, Deriv
     if ((long long)nx * ny * nz >= (1LL << 31)) { e = "lattice exceeds 2^31 - 1 nodes"; return false; }
     if (p->flow_model < LBPC_FLOW_NONE || p->flow_model > LBPC_FLOW_SRT) { e = "flow_model must be 0, 1 or 2"; return false; }
     if (p->enth_model != LBPC_ENTH_MRT && p->enth_model != LBPC_ENTH_SRT) { e = "enth_model must be 1 or 2"; return false; }
-    if (p->precision < LBPC_FP64 || p->precision > LBPC_BF16S) { e = "precision must be 0..3"; return false; }
+    if (p->precision < LBPC_FP64 || p->precision > LBPC_BF16S_G32) { e = "precision must be 0..5"; return false; }
     if (p->streaming != LBPC_PULL && p->streaming != LBPC_AA) { e = "streaming must be 0 or 1"; return false; }
     for (int f = 0; f < 6; f++)
         if (p->bc[f] < LBPC_PERIODIC || p->bc[f] > LBPC_ADIABATIC) { e = "bc codes must be 0..2"; return false; }
@@ -104,11 +104,16 @@ inline void fill_coef(Coef<C>& c, const lbpc_params& p, const Derived& d) {
     c.s_nu = (C)d.s_nu;
     c.s_pi = (C)d.s_pi;
     c.s_t = (C)d.s_t;
-    const bool shifted = p.precision == LBPC_FP16S || p.precision == LBPC_BF16S;
+    const bool gshifted = p.precision == LBPC_FP16S || p.precision == LBPC_BF16S;
+    const bool shifted = gshifted || p.precision == LBPC_FP16S_G32 || p.precision == LBPC_BF16S_G32;
     c.fshift0 = (C)(shifted ? 1.0 / 3.0 : 0.0);
     c.fshift1 = (C)(shifted ? 1.0 / 18.0 : 0.0);
     c.fshift2 = (C)(shifted ? 1.0 / 36.0 : 0.0);
-    c.gshift = (C)(shifted ? 0.5 * p.omega_T * p.Cp_ref * p.Tref : 0.0);
+    c.gshift = (C)(gshifted ? 0.5 * p.omega_T * p.Cp_ref * p.Tref : 0.0);
+    // M applied to the rest weights (1/3, 1/18 x 6, 1/36 x 12): rows 0, 1, 2 (Eq. 51)
+    c.frho = (C)(shifted ? 1.0 : 0.0);
+    c.fm1 = (C)(shifted ? -11.0 : 0.0);
+    c.fm2 = (C)(shifted ? 3.0 : 0.0);
 }
 
 // Kernel argument block of a validated parameter block; Tw[f] are the device (or host,

@@ -18,6 +18,7 @@ struct Coef {
     C s_e, s_eps, s_q, s_nu, s_pi, s_t;    // D3Q19 rates (Eq. 52)
     C fshift0, fshift1, fshift2;           // storage shifts of f: rest / axis / diagonal weight
     C gshift;                              // storage shift of g_1..6
+    C frho, fm1, fm2;  // moments 0, 1, 2 of the f shifts (1, -11, 3 when shifted, else 0)
 };
 
 struct Args {
@@ -72,7 +73,8 @@ struct Launchers {
                      double* Jpart, cudaStream_t);
     void (*adj_reverse)(const Args&, const void* lin, void* lout, const double* tape_e,
                         const void* tape_m, int wface, double* gtw, double* Lpart, cudaStream_t);
-    size_t store_bytes;    // bytes of one stored population value
+    size_t f_bytes;        // bytes of one stored f value
+    size_t g_bytes;        // bytes of one stored g value
     size_t compute_bytes;  // bytes of one compute-precision value (adjoint, tape)
 };
 
@@ -90,6 +92,8 @@ const Launchers& launchers_f64();
 const Launchers& launchers_f32();
 const Launchers& launchers_f16();
 const Launchers& launchers_bf16();
+const Launchers& launchers_f16g32();
+const Launchers& launchers_bf16g32();
 
 void finalize_reduction(const Args& a, const double* partial, const double* lines,
                         const double* face_area_inv, double nu_scale, double fd_scale,

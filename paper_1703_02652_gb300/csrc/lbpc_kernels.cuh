@@ -21,30 +21,59 @@
 namespace lbpc {
 
 // ---------------------------------------------------------------------------------
-// Storage codecs.  16-bit modes store the deviation from a fixed shift (the rest
-// weight of f, (omega_T / 2) Cp_ref T_ref for g) and compute in FP32.
+// Storage codecs.  Kernels compute on the stored representation r of a population: the
+// value itself for FP64/FP32, its deviation from a fixed shift (the rest weight of f,
+// (omega_T / 2) Cp_ref T_ref for g) for the 16-bit modes; the shift constants are folded
+// into the arithmetic (Coef::frho, fm1, fm2, gshift).  16-bit values are also snapped to
+// multiples of 2^-20 before rounding, so that a sum of six of them (each below 2 in
+// magnitude) is exact in FP32: the enthalpy channel then needs no compensated sums.
+// Only g needs the grid (enc_g); f is rounded plainly (enc).
 // ---------------------------------------------------------------------------------
 template <int P> struct Store;
 template <> struct Store<LBPC_FP64> {
     using T = double; using C = double;
+    static constexpr bool kGrid = false;
     static LBPC_HD C dec(T v, C) { return v; }
     static LBPC_HD T enc(C v, C) { return v; }
+    static LBPC_HD T enc_g(C v, C) { return v; }
+    static LBPC_HD C grid(C v) { return v; }
 };
 template <> struct Store<LBPC_FP32> {
     using T = float; using C = float;
+    static constexpr bool kGrid = false;
     static LBPC_HD C dec(T v, C) { return v; }
     static LBPC_HD T enc(C v, C) { return v; }
+    static LBPC_HD T enc_g(C v, C) { return v; }
+    static LBPC_HD C grid(C v) { return v; }
 };
+// (v + 12) - 12 rounds v to a multiple of ulp(12) = 2^-20 for |v| < 4.
+LBPC_HD float snap20(float v) { return (v + 12.0f) - 12.0f; }
 template <> struct Store<LBPC_FP16S> {
     using T = __half; using C = float;
-    static LBPC_HD C dec(T v, C s) { return __half2float(v) + s; }
-    static LBPC_HD T enc(C v, C s) { return __float2half_rn(v - s); }
+    static constexpr bool kGrid = true;
+    static LBPC_HD C dec(T v, C) { return __half2float(v); }
+    static LBPC_HD T enc(C v, C) { return __float2half_rn(v); }
+    static LBPC_HD T enc_g(C v, C) { return __float2half_rn(snap20(v)); }
+    static LBPC_HD C grid(C v) { return snap20(v); }
 };
 template <> struct Store<LBPC_BF16S> {
     using T = __nv_bfloat16; using C = float;
-    static LBPC_HD C dec(T v, C s) { return __bfloat162float(v) + s; }
-    static LBPC_HD T enc(C v, C s) { return __float2bfloat16_rn(v - s); }
+    static constexpr bool kGrid = true;
+    static LBPC_HD C dec(T v, C) { return __bfloat162float(v); }
+    static LBPC_HD T enc(C v, C) { return __float2bfloat16_rn(v); }
+    static LBPC_HD T enc_g(C v, C) { return __float2bfloat16_rn(snap20(v)); }
+    static LBPC_HD C grid(C v) { return snap20(v); }
 };
+
+// A storage mode fixes the precision of f (F) and of g (G): the four uniform modes, and
+// 16-bit f with FP32 g, which keeps the enthalpy populations (and the wall fluxes they
+// carry) at FP32 resolution for 140 instead of 116 bytes per node update.
+template <int P> struct Mode { static constexpr int F = P, G = P; };
+template <> struct Mode<LBPC_FP16S_G32> { static constexpr int F = LBPC_FP16S, G = LBPC_FP32; };
+template <> struct Mode<LBPC_BF16S_G32> { static constexpr int F = LBPC_BF16S, G = LBPC_FP32; };
+template <int P> using TF = typename Store<Mode<P>::F>::T;
+template <int P> using TG = typename Store<Mode<P>::G>::T;
+template <int P> using CT = typename Store<Mode<P>::F>::C;
 
 // Exact float -> double by integer operations (subnormal floats, below 1.2e-38, become
 // zero); keeps the conversions off the FP64 pipe, which on GB300 issues a few
@@ -78,6 +107,7 @@ LBPC_HD float d2f_trunc(double v) {
     return r;
 #endif
 }
+
 // Pairs of consecutive nodes along x: vector types and codecs of two values.
 template <class T> struct Vec2;
 template <> struct Vec2<double> { using type = double2; };
@@ -89,27 +119,35 @@ template <int P> struct Pair;
 template <> struct Pair<LBPC_FP64> {
     static LBPC_HD void dec(double2 v, double, double& a, double& b) { a = v.x; b = v.y; }
     static LBPC_HD double2 enc(double a, double b, double) { return make_double2(a, b); }
+    static LBPC_HD double2 enc_g(double a, double b, double) { return make_double2(a, b); }
 };
 template <> struct Pair<LBPC_FP32> {
     static LBPC_HD void dec(float2 v, float, float& a, float& b) { a = v.x; b = v.y; }
     static LBPC_HD float2 enc(float a, float b, float) { return make_float2(a, b); }
+    static LBPC_HD float2 enc_g(float a, float b, float) { return make_float2(a, b); }
 };
 template <> struct Pair<LBPC_FP16S> {
-    static LBPC_HD void dec(__half2 v, float s, float& a, float& b) {
+    static LBPC_HD void dec(__half2 v, float, float& a, float& b) {
         const float2 t = __half22float2(v);
-        a = t.x + s;
-        b = t.y + s;
+        a = t.x;
+        b = t.y;
     }
-    static LBPC_HD __half2 enc(float a, float b, float s) { return __floats2half2_rn(a - s, b - s); }
+    static LBPC_HD __half2 enc(float a, float b, float) { return __floats2half2_rn(a, b); }
+    static LBPC_HD __half2 enc_g(float a, float b, float) {
+        return __floats2half2_rn(snap20(a), snap20(b));
+    }
 };
 template <> struct Pair<LBPC_BF16S> {
-    static LBPC_HD void dec(__nv_bfloat162 v, float s, float& a, float& b) {
+    static LBPC_HD void dec(__nv_bfloat162 v, float, float& a, float& b) {
         const float2 t = __bfloat1622float2(v);
-        a = t.x + s;
-        b = t.y + s;
+        a = t.x;
+        b = t.y;
     }
-    static LBPC_HD __nv_bfloat162 enc(float a, float b, float s) {
-        return __floats2bfloat162_rn(a - s, b - s);
+    static LBPC_HD __nv_bfloat162 enc(float a, float b, float) {
+        return __floats2bfloat162_rn(a, b);
+    }
+    static LBPC_HD __nv_bfloat162 enc_g(float a, float b, float) {
+        return __floats2bfloat162_rn(snap20(a), snap20(b));
     }
 };
 
@@ -189,11 +227,11 @@ LBPC_HD C fshift(const Coef<C>& k, int q) {
     return q == 0 ? k.fshift0 : (q < 7 ? k.fshift1 : k.fshift2);
 }
 
-// Anti-bounce-back source of a g population entering through face `face` (isothermal).
+// Anti-bounce-back source of a g population entering through face `face` (isothermal),
+// in the representation: g_in = -g*_out + omega_T Cp_ref T_w, i.e. r_in = -r_out + this.
 template <class C>
-LBPC_HD C abb_source(const Args& a, const Coef<C>& k, int face, int x, int y,
-                                        int z) {
-    return k.wT_cref * (C)a.Tw[face][face_index(a, face, x, y, z)];
+LBPC_HD C abb_source(const Args& a, const Coef<C>& k, int face, int x, int y, int z) {
+    return k.wT_cref * (C)a.Tw[face][face_index(a, face, x, y, z)] - C(2) * k.gshift;
 }
 
 // ---------------------------------------------------------------------------------
@@ -263,7 +301,7 @@ LBPC_HD void gather_g(const Args& a, const NB& b, int n, int x, int y, int z,
             if constexpr (LAYOUT == LAYOUT_PULL) slot = w ? op : q;                      \
             else slot = w ? q : op;                                                     \
             C v = S::dec(ldv<P, LAYOUT, NC>(gs + (size_t)(slot - 1) * N + idx), k.gshift);     \
-            if (w && a.wall_iso[q - 1]) v = -v + abb_source(a, k, q - 1, x, y, z);       \
+            if (w && a.wall_iso[q - 1]) v = S::grid(-v + abb_source(a, k, q - 1, x, y, z)); \
             g[q] = v;                                                                   \
         }                                                                               \
     }
@@ -310,7 +348,7 @@ LBPC_HD void scatter_g(const Args& a, const NB& b, int n, int x, int y, int z,
     const size_t N = (size_t)a.N;
 #define LBPC_SG(q, ex, ey, ez, op)                                                       \
     {                                                                                   \
-        const auto v = S::enc(g[q], k.gshift);                                          \
+        const auto v = S::enc_g(g[q], k.gshift);                                        \
         g[q] = S::dec(v, k.gshift);                                                     \
         if constexpr (KIND == STEP_PULL) {                                              \
             gd[(size_t)(q - 1) * N + n] = v;                                                  \
@@ -321,8 +359,8 @@ LBPC_HD void scatter_g(const Args& a, const NB& b, int n, int x, int y, int z,
             if (w) {                                                                    \
                 auto vb = v;                                                            \
                 if (a.wall_iso[op - 1])                                                 \
-                    vb = S::enc(-S::dec(v, k.gshift) + abb_source(a, k, op - 1, x, y, z), \
-                                k.gshift);                                              \
+                    vb = S::enc_g(-S::dec(v, k.gshift) + abb_source(a, k, op - 1, x, y, z), \
+                                  k.gshift);                                            \
                 gd[(size_t)(op - 1) * N + n] = vb;                                            \
             } else {                                                                    \
                 gd[(size_t)(q - 1) * N + n + b.template off<-(ex), -(ey), -(ez)>()] = v;             \
@@ -366,7 +404,7 @@ LBPC_HD void flow_macro(const C* f, const Coef<C>& k, C T, C fl, C& rho, C& jx,
                                            C& Fz) {
     rho = ((f[0] + (f[1] + f[2])) + ((f[3] + f[4]) + (f[5] + f[6]))) +
           (((f[7] + f[8]) + (f[9] + f[10])) + ((f[11] + f[12]) + (f[13] + f[14])) +
-           ((f[15] + f[16]) + (f[17] + f[18])));
+           ((f[15] + f[16]) + (f[17] + f[18]))) + k.frho;
     jx = (f[1] - f[2]) + (f[7] - f[8] + f[9] - f[10]) + (f[11] - f[12] + f[13] - f[14]);
     jy = (f[3] - f[4]) + (f[7] + f[8] - f[9] - f[10]) + (f[15] - f[16] + f[17] - f[18]);
     jz = (f[5] - f[6]) + (f[11] + f[12] - f[13] - f[14]) + (f[15] + f[16] - f[17] - f[18]);
@@ -404,15 +442,15 @@ LBPC_HD void collide_flow(C* f, const Coef<C>& k, C T, C fl, C& ux, C& uy, C& uz
     const C yz_p = (f[15] - f[16]) - (f[17] - f[18]);
     const C sax = a1 + a3 + a5, sdg = sxy + sxz + syz;
 
-    const C rho = f[0] + sax + sdg;
+    const C rho = f[0] + sax + sdg + k.frho;
     const C jx = b1 + xy_x + xz_x, jy = b3 + xy_y + yz_y, jz = b5 + xz_z + yz_z;
     rho_o = rho;
     jx_o = jx;
     jy_o = jy;
     jz_o = jz;
     // non-conserved moments (rows 1, 2, 4, 6, 8-18 of Eq. 51)
-    const C m1 = C(-30) * f[0] - C(11) * sax + C(8) * sdg;
-    const C m2 = C(12) * f[0] - C(4) * sax + sdg;
+    const C m1 = C(-30) * f[0] - C(11) * sax + C(8) * sdg + k.fm1;
+    const C m2 = C(12) * f[0] - C(4) * sax + sdg + k.fm2;
     const C m4 = C(-4) * b1 + xy_x + xz_x;
     const C m6 = C(-4) * b3 + xy_y + yz_y;
     const C m8 = C(-4) * b5 + xz_z + yz_z;
@@ -498,7 +536,7 @@ template <class C>
 LBPC_HD void collide_enth(C* g, const Coef<C>& k, C T, C fl, C ux, C uy,
                                              C uz) {
     const C Cp = fl * k.Cpl + (C(1) - fl) * k.Cps;
-    const C cT = k.wa_cref * T;       // even part of g^eq_a (Eq. 7)
+    const C cT = k.wa_cref * T - k.gshift;  // even part of g^eq_a (Eq. 7), representation
     const C vT = C(0.5) * Cp * T;     // (omega_a / c_sT^2) Cp T = Cp T / 2
     const C e1 = cT + vT * ux, e2 = cT - vT * ux;
     const C e3 = cT + vT * uy, e4 = cT - vT * uy;
@@ -543,23 +581,32 @@ LBPC_HD void sum6_pair(const float* g, float& hi, float& lo) {
     two_sum(hi, g[5], hi, e); lo += e;
     two_sum(hi, g[6], hi, e); lo += e;
 }
-// e' + sum g_a
-LBPC_HD double excess_plus(double ep, const float* g) {
-    float hi, lo;
-    sum6_pair(g, hi, lo);
-    return (ep + f2d_exact(hi)) + f2d_exact(lo);
+// e' + sum g_a and e - sum g_a.  FP64: plain FP64 sums.  FP32 storage: exact FP32 pair
+// sums (TwoSum).  16-bit storage: the six values lie on a 2^-20 grid, so a plain FP32
+// sum is already exact.
+template <int P>
+LBPC_HD double excess_plus(double ep, const typename Store<P>::C* g) {
+    if constexpr (P == LBPC_FP64) {
+        return ep + g[1] + g[2] + g[3] + g[4] + g[5] + g[6];
+    } else if constexpr (Store<P>::kGrid) {
+        return ep + f2d_exact(((g[1] + g[2]) + (g[3] + g[4])) + (g[5] + g[6]));
+    } else {
+        float hi, lo;
+        sum6_pair(g, hi, lo);
+        return (ep + f2d_exact(hi)) + f2d_exact(lo);
+    }
 }
-LBPC_HD double excess_plus(double ep, const double* g) {
-    return ep + g[1] + g[2] + g[3] + g[4] + g[5] + g[6];
-}
-// e - sum g_a
-LBPC_HD double excess_minus(double e, const float* g) {
-    float hi, lo;
-    sum6_pair(g, hi, lo);
-    return (e - f2d_exact(hi)) - f2d_exact(lo);
-}
-LBPC_HD double excess_minus(double e, const double* g) {
-    return e - g[1] - g[2] - g[3] - g[4] - g[5] - g[6];
+template <int P>
+LBPC_HD double excess_minus(double e, const typename Store<P>::C* g) {
+    if constexpr (P == LBPC_FP64) {
+        return e - g[1] - g[2] - g[3] - g[4] - g[5] - g[6];
+    } else if constexpr (Store<P>::kGrid) {
+        return e - f2d_exact(((g[1] + g[2]) + (g[3] + g[4])) + (g[5] + g[6]));
+    } else {
+        float hi, lo;
+        sum6_pair(g, hi, lo);
+        return (e - f2d_exact(hi)) - f2d_exact(lo);
+    }
 }
 
 // ---------------------------------------------------------------------------------
@@ -575,12 +622,11 @@ template <> struct KindLayout<STEP_AA_ODD> { static constexpr int value = LAYOUT
 // One time step of node (x, y, z): gather (stream in, with wall rules), Eq. 2 inversion,
 // flow collision, enthalpy collision, scatter, FP64 rest channel update.
 template <int P, int KIND, bool FLOW, bool TAPE = false>
-LBPC_HD void step_node(const Args& a, int x, int y, int z, const typename Store<P>::T* fs,
-                       typename Store<P>::T* fd, const typename Store<P>::T* gs,
-                       typename Store<P>::T* gd, double* hp, double* tape_e = nullptr,
-                       typename Store<P>::C* tape_m = nullptr) {
-    using S = Store<P>;
-    using C = typename S::C;
+LBPC_HD void step_node(const Args& a, int x, int y, int z, const TF<P>* fs,
+                       TF<P>* fd, const TG<P>* gs,
+                       TG<P>* gd, double* hp, double* tape_e = nullptr,
+                       CT<P>* tape_m = nullptr) {
+    using C = CT<P>;
     const Coef<C>& k = coef<C>(a);
     const int n = x + a.nx * (y + a.ny * z);
     constexpr int LAYOUT = KindLayout<KIND>::value;
@@ -591,13 +637,13 @@ LBPC_HD void step_node(const Args& a, int x, int y, int z, const typename Store<
 
     C f[19], g[7];
     if (interior) {
-        if constexpr (FLOW) gather_f<P, LAYOUT, NC>(a, bi, n, fs, f);
-        gather_g<P, LAYOUT, NC>(a, bi, n, x, y, z, gs, g);
+        if constexpr (FLOW) gather_f<Mode<P>::F, LAYOUT, NC>(a, bi, n, fs, f);
+        gather_g<Mode<P>::G, LAYOUT, NC>(a, bi, n, x, y, z, gs, g);
     } else {
-        if constexpr (FLOW) gather_f<P, LAYOUT, NC>(a, b, n, fs, f);
-        gather_g<P, LAYOUT, NC>(a, b, n, x, y, z, gs, g);
+        if constexpr (FLOW) gather_f<Mode<P>::F, LAYOUT, NC>(a, b, n, fs, f);
+        gather_g<Mode<P>::G, LAYOUT, NC>(a, b, n, x, y, z, gs, g);
     }
-    const double e = excess_plus(hp[n], g);  // h - h_s
+    const double e = excess_plus<Mode<P>::G>(hp[n], g);  // h - h_s
 
     C T, fl;
     invert_excess(k, e, T, fl);
@@ -614,13 +660,13 @@ LBPC_HD void step_node(const Args& a, int x, int y, int z, const typename Store<
     }
     collide_enth(g, k, T, fl, ux, uy, uz);
     if (interior) {
-        if constexpr (FLOW) scatter_f<P, KIND>(a, bi, n, fd, f);
-        scatter_g<P, KIND>(a, bi, n, x, y, z, gd, g);
+        if constexpr (FLOW) scatter_f<Mode<P>::F, KIND>(a, bi, n, fd, f);
+        scatter_g<Mode<P>::G, KIND>(a, bi, n, x, y, z, gd, g);
     } else {
-        if constexpr (FLOW) scatter_f<P, KIND>(a, b, n, fd, f);
-        scatter_g<P, KIND>(a, b, n, x, y, z, gd, g);
+        if constexpr (FLOW) scatter_f<Mode<P>::F, KIND>(a, b, n, fd, f);
+        scatter_g<Mode<P>::G, KIND>(a, b, n, x, y, z, gd, g);
     }
-    hp[n] = excess_minus(e, g);
+    hp[n] = excess_minus<Mode<P>::G>(e, g);
 }
 
 
@@ -629,14 +675,18 @@ LBPC_HD void step_node(const Args& a, int x, int y, int z, const typename Store<
 // x-face rules applied by selects on the lanes at x = 0 / x = nx - 1; every store is a
 // pair.  Requires even nx.
 template <int P, bool FLOW>
-LBPC_HD void step_pair_pull(const Args& a, int x0, int y, int z, const typename Store<P>::T* fs,
-                            typename Store<P>::T* fd, const typename Store<P>::T* gs,
-                            typename Store<P>::T* gd, double* hp) {
-    using S = Store<P>;
-    using T = typename S::T;
-    using C = typename S::C;
-    using V = typename Vec2<T>::type;
-    using PR = Pair<P>;
+LBPC_HD void step_pair_pull(const Args& a, int x0, int y, int z, const TF<P>* fs,
+                            TF<P>* fd, const TG<P>* gs,
+                            TG<P>* gd, double* hp) {
+    using SF = Store<Mode<P>::F>;
+    using SG = Store<Mode<P>::G>;
+    using TFt = typename SF::T;
+    using TGt = typename SG::T;
+    using C = CT<P>;
+    using VF = typename Vec2<TFt>::type;
+    using VG = typename Vec2<TGt>::type;
+    using PRF = Pair<Mode<P>::F>;
+    using PRG = Pair<Mode<P>::G>;
     const Coef<C>& k = coef<C>(a);
     const size_t N = (size_t)a.N;
     const int sy = a.nx, sz = a.nx * a.ny;
@@ -652,18 +702,18 @@ LBPC_HD void step_pair_pull(const Args& a, int x0, int y, int z, const typename 
         {                                                                               \
             const int oyz = -(ey) * sy - (ez) * sz;                                     \
             const C sh = fshift(k, q);                                                  \
-            const T* pl = fs + (size_t)q * N;                                           \
+            const TFt* pl = fs + (size_t)q * N;                                           \
             if constexpr ((ex) == 0) {                                                  \
-                PR::dec(ld_any<true>(reinterpret_cast<const V*>(pl + n0 + oyz)),             \
+                PRF::dec(ld_any<true>(reinterpret_cast<const VF*>(pl + n0 + oyz)),             \
                         sh, f0[q], f1[q]);                                              \
             } else if constexpr ((ex) == 1) {                                           \
-                const T* p0 = wlo ? fs + (size_t)op * N + n0 : pl + up0 + oyz;          \
-                f0[q] = S::dec(ldv<P, LAYOUT_PULL, true>(p0), sh);                      \
-                f1[q] = S::dec(ldv<P, LAYOUT_PULL, true>(pl + n0 + oyz), sh);           \
+                const TFt* p0 = wlo ? fs + (size_t)op * N + n0 : pl + up0 + oyz;          \
+                f0[q] = SF::dec(ldv<Mode<P>::F, LAYOUT_PULL, true>(p0), sh);                      \
+                f1[q] = SF::dec(ldv<Mode<P>::F, LAYOUT_PULL, true>(pl + n0 + oyz), sh);           \
             } else {                                                                    \
-                const T* p1 = whi ? fs + (size_t)op * N + n1 : pl + up1 + oyz;          \
-                f0[q] = S::dec(ldv<P, LAYOUT_PULL, true>(pl + n1 + oyz), sh);           \
-                f1[q] = S::dec(ldv<P, LAYOUT_PULL, true>(p1), sh);                      \
+                const TFt* p1 = whi ? fs + (size_t)op * N + n1 : pl + up1 + oyz;          \
+                f0[q] = SF::dec(ldv<Mode<P>::F, LAYOUT_PULL, true>(pl + n1 + oyz), sh);           \
+                f1[q] = SF::dec(ldv<Mode<P>::F, LAYOUT_PULL, true>(p1), sh);                      \
             }                                                                           \
         }
         LBPC_Q19(LBPC_PF)
@@ -672,28 +722,28 @@ LBPC_HD void step_pair_pull(const Args& a, int x0, int y, int z, const typename 
 #define LBPC_PG(q, ex, ey, ez, op)                                                       \
     {                                                                                   \
         const int oyz = -(ey) * sy - (ez) * sz;                                         \
-        const T* pl = gs + (size_t)(q - 1) * N;                                         \
+        const TGt* pl = gs + (size_t)(q - 1) * N;                                         \
         if constexpr ((ex) == 0) {                                                      \
-            PR::dec(ld_any<true>(reinterpret_cast<const V*>(pl + n0 + oyz)),                 \
+            PRG::dec(ld_any<true>(reinterpret_cast<const VG*>(pl + n0 + oyz)),                 \
                     k.gshift, g0[q], g1[q]);                                            \
         } else if constexpr ((ex) == 1) {                                               \
-            const T* p0 = wlo ? gs + (size_t)(op - 1) * N + n0 : pl + up0 + oyz;        \
-            C v = S::dec(ldv<P, LAYOUT_PULL, true>(p0), k.gshift);                      \
-            if (wlo && a.wall_iso[0]) v = -v + abb_source(a, k, 0, x0, y, z);           \
+            const TGt* p0 = wlo ? gs + (size_t)(op - 1) * N + n0 : pl + up0 + oyz;        \
+            C v = SG::dec(ldv<Mode<P>::G, LAYOUT_PULL, true>(p0), k.gshift);                      \
+            if (wlo && a.wall_iso[0]) v = SG::grid(-v + abb_source(a, k, 0, x0, y, z)); \
             g0[q] = v;                                                                  \
-            g1[q] = S::dec(ldv<P, LAYOUT_PULL, true>(pl + n0 + oyz), k.gshift);         \
+            g1[q] = SG::dec(ldv<Mode<P>::G, LAYOUT_PULL, true>(pl + n0 + oyz), k.gshift);         \
         } else {                                                                        \
-            const T* p1 = whi ? gs + (size_t)(op - 1) * N + n1 : pl + up1 + oyz;        \
-            C v = S::dec(ldv<P, LAYOUT_PULL, true>(p1), k.gshift);                      \
-            if (whi && a.wall_iso[1]) v = -v + abb_source(a, k, 1, x0 + 1, y, z);       \
+            const TGt* p1 = whi ? gs + (size_t)(op - 1) * N + n1 : pl + up1 + oyz;        \
+            C v = SG::dec(ldv<Mode<P>::G, LAYOUT_PULL, true>(p1), k.gshift);                      \
+            if (whi && a.wall_iso[1]) v = SG::grid(-v + abb_source(a, k, 1, x0 + 1, y, z)); \
             g1[q] = v;                                                                  \
-            g0[q] = S::dec(ldv<P, LAYOUT_PULL, true>(pl + n1 + oyz), k.gshift);         \
+            g0[q] = SG::dec(ldv<Mode<P>::G, LAYOUT_PULL, true>(pl + n1 + oyz), k.gshift);         \
         }                                                                               \
     }
     LBPC_Q7(LBPC_PG)
 #undef LBPC_PG
     const double2 ep = ld_any<true>(reinterpret_cast<const double2*>(hp + n0));
-    const double e0 = excess_plus(ep.x, g0), e1 = excess_plus(ep.y, g1);
+    const double e0 = excess_plus<Mode<P>::G>(ep.x, g0), e1 = excess_plus<Mode<P>::G>(ep.y, g1);
     C T0, fl0, T1, fl1;
     invert_excess(k, e0, T0, fl0);
     invert_excess(k, e1, T1, fl1);
@@ -703,7 +753,7 @@ LBPC_HD void step_pair_pull(const Args& a, int x0, int y, int z, const typename 
         collide_flow(f0, k, T0, fl0, ux0, uy0, uz0, r, jx, jy, jz);
         collide_flow(f1, k, T1, fl1, ux1, uy1, uz1, r, jx, jy, jz);
 #define LBPC_SPF(q, ex, ey, ez, op)                                                      \
-        *reinterpret_cast<V*>(fd + (size_t)q * N + n0) = PR::enc(f0[q], f1[q], fshift(k, q));
+        *reinterpret_cast<VF*>(fd + (size_t)q * N + n0) = PRF::enc(f0[q], f1[q], fshift(k, q));
         LBPC_Q19(LBPC_SPF)
 #undef LBPC_SPF
     }
@@ -711,30 +761,29 @@ LBPC_HD void step_pair_pull(const Args& a, int x0, int y, int z, const typename 
     collide_enth(g1, k, T1, fl1, ux1, uy1, uz1);
 #define LBPC_SPG(q, ex, ey, ez, op)                                                      \
     {                                                                                   \
-        const V v = PR::enc(g0[q], g1[q], k.gshift);                                    \
-        *reinterpret_cast<V*>(gd + (size_t)(q - 1) * N + n0) = v;                        \
-        PR::dec(v, k.gshift, g0[q], g1[q]);                                             \
+        const VG v = PRG::enc_g(g0[q], g1[q], k.gshift);                                \
+        *reinterpret_cast<VG*>(gd + (size_t)(q - 1) * N + n0) = v;                       \
+        PRG::dec(v, k.gshift, g0[q], g1[q]);                                            \
     }
     LBPC_Q7(LBPC_SPG)
 #undef LBPC_SPG
-    *reinterpret_cast<double2*>(hp + n0) = make_double2(excess_minus(e0, g0), excess_minus(e1, g1));
+    *reinterpret_cast<double2*>(hp + n0) = make_double2(excess_minus<Mode<P>::G>(e0, g0), excess_minus<Mode<P>::G>(e1, g1));
 }
 
 // Macroscopic state of node n and its contributions to the diagnostics sums
 // (acc: sum f_l, sum h, sum rho, -x wall flux, -x wall gradient, non-finite count).
 template <int P, int LAYOUT, bool FLOW>
-LBPC_HD void macro_node(const Args& a, int n, const typename Store<P>::T* fs,
-                        const typename Store<P>::T* gs, const double* hp, const MacroOut& out,
+LBPC_HD void macro_node(const Args& a, int n, const TF<P>* fs,
+                        const TG<P>* gs, const double* hp, const MacroOut& out,
                         double* acc) {
-    using S = Store<P>;
-    using C = typename S::C;
+    using C = CT<P>;
     const Coef<C>& k = coef<C>(a);
     const int x = n % a.nx, y = (n / a.nx) % a.ny, z = n / (a.nx * a.ny);
     const Nb b = make_nb(a, x, y, z);
     C f[19], g[7];
-    if constexpr (FLOW) gather_f<P, LAYOUT, true>(a, b, n, fs, f);
-    gather_g<P, LAYOUT, true>(a, b, n, x, y, z, gs, g);
-    const double e = excess_plus(hp[n], g);
+    if constexpr (FLOW) gather_f<Mode<P>::F, LAYOUT, true>(a, b, n, fs, f);
+    gather_g<Mode<P>::G, LAYOUT, true>(a, b, n, x, y, z, gs, g);
+    const double e = excess_plus<Mode<P>::G>(hp[n], g);
     const double h = a.hs + e;
     C T, fl;
     invert_excess(k, e, T, fl);
@@ -756,7 +805,7 @@ LBPC_HD void macro_node(const Args& a, int n, const typename Store<P>::T* fs,
         acc[2] += (double)rho;
         if (x == 0) {
             const double Tw = a.Tw[0][y + a.ny * z];
-            if (a.wall_iso[0]) acc[3] += 2.0 * (double)g[1] - (double)k.wT_cref * Tw;
+            if (a.wall_iso[0]) acc[3] += 2.0 * ((double)g[1] + (double)k.gshift) - (double)k.wT_cref * Tw;
             acc[4] += (Tw - (double)T) * 2.0;
         }
         if (!isfinite(h) || !isfinite((double)rho)) acc[5] += 1.0;
@@ -788,9 +837,8 @@ LBPC_HD double state_g(const Args& a, const Coef<C>& k, const double* Qg, const 
 // downwind neighbour lies behind a wall feed the node's own bounce-back.
 template <int P, int LAYOUT, bool FLOW>
 LBPC_HD void init_node(const Args& a, int x, int y, int z, const double* Qf, const double* Qg,
-                       const double* h0, typename Store<P>::T* fd, typename Store<P>::T* gd) {
-    using S = Store<P>;
-    using C = typename S::C;
+                       const double* h0, TF<P>* fd, TG<P>* gd) {
+    using C = CT<P>;
     const Coef<C>& k = coef<C>(a);
     const int n = x + a.nx * (y + a.ny * z);
     const Nb b = make_nb(a, x, y, z);
@@ -805,7 +853,7 @@ LBPC_HD void init_node(const Args& a, int x, int y, int z, const double* Qf, con
                 v = w ? state_f<C>(Qf, N, op, n)                                        \
                       : state_f<C>(Qf, N, q, n + b.template off<-(ex), -(ey), -(ez)>());       \
             }                                                                           \
-            fd[(size_t)q * N + n] = S::enc((C)v, fshift(k, q));                         \
+            fd[(size_t)q * N + n] = Store<Mode<P>::F>::enc((C)(v - (double)fshift(k, q)), C(0)); \
         }
         LBPC_Q19(LBPC_IF)
 #undef LBPC_IF
@@ -824,7 +872,7 @@ LBPC_HD void init_node(const Args& a, int x, int y, int z, const double* Qf, con
                 v = state_g(a, k, Qg, h0, q, n + b.template off<-(ex), -(ey), -(ez)>());       \
             }                                                                           \
         }                                                                               \
-        gd[(size_t)(q - 1) * N + n] = S::enc((C)v, k.gshift);                                 \
+        gd[(size_t)(q - 1) * N + n] = Store<Mode<P>::G>::enc_g((C)(v - (double)k.gshift), C(0)); \
     }
     LBPC_Q7(LBPC_IG)
 #undef LBPC_IG
@@ -833,8 +881,8 @@ LBPC_HD void init_node(const Args& a, int x, int y, int z, const double* Qf, con
 // e' = h - h_s - sum_a g_a(gathered), so that the stored state reproduces h.
 template <int P, int LAYOUT>
 LBPC_HD void init_hprime_node(const Args& a, int x, int y, int z, const double* Qg,
-                              const double* h0, const typename Store<P>::T* gs, double* hp) {
-    using C = typename Store<P>::C;
+                              const double* h0, const TG<P>* gs, double* hp) {
+    using C = CT<P>;
     const int n = x + a.nx * (y + a.ny * z);
     const Nb b = make_nb(a, x, y, z);
     double h;
@@ -845,27 +893,29 @@ LBPC_HD void init_hprime_node(const Args& a, int x, int y, int z, const double* 
         h = h0[n];
     }
     C g[7];
-    gather_g<P, LAYOUT, true>(a, b, n, x, y, z, gs, g);
-    hp[n] = excess_minus(h - a.hs, g);
+    gather_g<Mode<P>::G, LAYOUT, true>(a, b, n, x, y, z, gs, g);
+    hp[n] = excess_minus<Mode<P>::G>(h - a.hs, g);
 }
 
 // Pre-collision populations of node (x, y, z) in FP64 (g_0 = h' = h_s + e').
 template <int P, int LAYOUT, bool FLOW>
-LBPC_HD void dist_node(const Args& a, int x, int y, int z, const typename Store<P>::T* fs,
-                       const typename Store<P>::T* gs, const double* hp, double* Qf, double* Qg) {
-    using C = typename Store<P>::C;
+LBPC_HD void dist_node(const Args& a, int x, int y, int z, const TF<P>* fs,
+                       const TG<P>* gs, const double* hp, double* Qf, double* Qg) {
+    using C = CT<P>;
     const int n = x + a.nx * (y + a.ny * z);
     const Nb b = make_nb(a, x, y, z);
     const size_t N = (size_t)a.N;
+    const Coef<C>& k = coef<C>(a);
     C g[7];
-    gather_g<P, LAYOUT, true>(a, b, n, x, y, z, gs, g);
-    Qg[n] = a.hs + hp[n];
-    for (int q = 1; q < 7; q++) Qg[(size_t)q * N + n] = (double)g[q];
+    gather_g<Mode<P>::G, LAYOUT, true>(a, b, n, x, y, z, gs, g);
+    const double gs_ = (double)k.gshift;
+    Qg[n] = a.hs + hp[n] - 6.0 * gs_;
+    for (int q = 1; q < 7; q++) Qg[(size_t)q * N + n] = (double)g[q] + gs_;
     if constexpr (FLOW) {
         if (Qf) {
             C f[19];
-            gather_f<P, LAYOUT, true>(a, b, n, fs, f);
-            for (int q = 0; q < 19; q++) Qf[(size_t)q * N + n] = (double)f[q];
+            gather_f<Mode<P>::F, LAYOUT, true>(a, b, n, fs, f);
+            for (int q = 0; q < 19; q++) Qf[(size_t)q * N + n] = (double)f[q] + (double)fshift(k, q);
         }
     }
 }
@@ -1065,16 +1115,16 @@ LBPC_HD C collide_adjoint(const Coef<C>& k, double e, C rho, C jx, C jy, C jz, C
 // Adjoint seed at the final state: lambda_g = d f_l / dh on every g population,
 // lambda_f = 0; returns d f_l / dL and writes f_l (for J).
 template <int P, bool FLOW>
-LBPC_HD typename Store<P>::C adj_seed_node(const Args& a, int x, int y, int z,
-                                           const typename Store<P>::T* gs, const double* hp,
-                                           typename Store<P>::C* lam, double& fl_out) {
-    using C = typename Store<P>::C;
+LBPC_HD CT<P> adj_seed_node(const Args& a, int x, int y, int z,
+                                           const TG<P>* gs, const double* hp,
+                                           CT<P>* lam, double& fl_out) {
+    using C = CT<P>;
     const Coef<C>& k = coef<C>(a);
     const int n = x + a.nx * (y + a.ny * z);
     const Nb b = make_nb(a, x, y, z);
     C g[7];
-    gather_g<P, LAYOUT_PULL, true>(a, b, n, x, y, z, gs, g);
-    const double e = excess_plus(hp[n], g);
+    gather_g<Mode<P>::G, LAYOUT_PULL, true>(a, b, n, x, y, z, gs, g);
+    const double e = excess_plus<Mode<P>::G>(hp[n], g);
     C T, fl, dTde, dfde, dTdL, dfdL;
     invert_excess_d(k, e, T, fl, dTde, dfde, dTdL, dfdL);
     const size_t N = (size_t)a.N;
@@ -1089,12 +1139,12 @@ LBPC_HD typename Store<P>::C adj_seed_node(const Args& a, int x, int y, int z,
 // downwind neighbours, with the transposed wall rules) then transposed collision with
 // the tape of step n.  Accumulates dJ/dT_w of face `wface` and returns the dJ/dL part.
 template <int P, bool FLOW, class NB>
-LBPC_HD typename Store<P>::C adj_reverse_node(const Args& a, const NB& b, int x, int y, int z,
-                                              const typename Store<P>::C* lin,
-                                              typename Store<P>::C* lout, const double* tape_e,
-                                              const typename Store<P>::C* tape_m, int wface,
+LBPC_HD CT<P> adj_reverse_node(const Args& a, const NB& b, int x, int y, int z,
+                                              const CT<P>* lin,
+                                              CT<P>* lout, const double* tape_e,
+                                              const CT<P>* tape_m, int wface,
                                               double* gtw) {
-    using C = typename Store<P>::C;
+    using C = CT<P>;
     const Coef<C>& k = coef<C>(a);
     const int n = x + a.nx * (y + a.ny * z);
     const size_t N = (size_t)a.N;
@@ -1154,8 +1204,8 @@ LBPC_HD typename Store<P>::C adj_reverse_node(const Args& a, const NB& b, int x,
 
 template <int P, int KIND, bool FLOW>
 __global__ void __launch_bounds__(STEP_THREADS)
-k_step(const __grid_constant__ Args a, const typename Store<P>::T* fs, typename Store<P>::T* fd,
-       const typename Store<P>::T* gs, typename Store<P>::T* gd, double* __restrict__ hp) {
+k_step(const __grid_constant__ Args a, const TF<P>* fs, TF<P>* fd,
+       const TG<P>* gs, TG<P>* gd, double* __restrict__ hp) {
     LBPC_NODE_XYZ
     step_node<P, KIND, FLOW>(a, x, y, z, fs, fd, gs, gd, hp);
 }
@@ -1165,8 +1215,8 @@ k_step(const __grid_constant__ Args a, const typename Store<P>::T* fs, typename 
 // from the y and z faces take the paired path; others run the per-node path twice.
 template <int P, bool FLOW>
 __global__ void __launch_bounds__(STEP_THREADS)
-k_step_pull_x2(const __grid_constant__ Args a, const typename Store<P>::T* fs,
-               typename Store<P>::T* fd, const typename Store<P>::T* gs, typename Store<P>::T* gd,
+k_step_pull_x2(const __grid_constant__ Args a, const TF<P>* fs,
+               TF<P>* fd, const TG<P>* gs, TG<P>* gd,
                double* __restrict__ hp) {
     const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -1194,8 +1244,8 @@ __device__ __forceinline__ T warp_sum(T v) {
 // (grid-stride over nodes; one partial row per block, summed later in a fixed order).
 template <int P, int LAYOUT, bool FLOW>
 __global__ void __launch_bounds__(RED_THREADS)
-k_macro(const __grid_constant__ Args a, const typename Store<P>::T* __restrict__ fs,
-        const typename Store<P>::T* __restrict__ gs, const double* __restrict__ hp,
+k_macro(const __grid_constant__ Args a, const TF<P>* __restrict__ fs,
+        const TG<P>* __restrict__ gs, const double* __restrict__ hp,
         const MacroOut out) {
     double acc[NRED] = {0, 0, 0, 0, 0, 0};
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < a.N; n += gridDim.x * blockDim.x)
@@ -1219,7 +1269,7 @@ k_macro(const __grid_constant__ Args a, const typename Store<P>::T* __restrict__
 template <int P, int LAYOUT, bool FLOW>
 __global__ void __launch_bounds__(STEP_THREADS)
 k_init(const __grid_constant__ Args a, const double* __restrict__ Qf, const double* __restrict__ Qg,
-       const double* __restrict__ h0, typename Store<P>::T* fd, typename Store<P>::T* gd) {
+       const double* __restrict__ h0, TF<P>* fd, TG<P>* gd) {
     LBPC_NODE_XYZ
     init_node<P, LAYOUT, FLOW>(a, x, y, z, Qf, Qg, h0, fd, gd);
 }
@@ -1227,7 +1277,7 @@ k_init(const __grid_constant__ Args a, const double* __restrict__ Qf, const doub
 template <int P, int LAYOUT>
 __global__ void __launch_bounds__(STEP_THREADS)
 k_init_hprime(const __grid_constant__ Args a, const double* __restrict__ Qg,
-              const double* __restrict__ h0, const typename Store<P>::T* __restrict__ gs,
+              const double* __restrict__ h0, const TG<P>* __restrict__ gs,
               double* __restrict__ hp) {
     LBPC_NODE_XYZ
     init_hprime_node<P, LAYOUT>(a, x, y, z, Qg, h0, gs, hp);
@@ -1235,8 +1285,8 @@ k_init_hprime(const __grid_constant__ Args a, const double* __restrict__ Qg,
 
 template <int P, int LAYOUT, bool FLOW>
 __global__ void __launch_bounds__(STEP_THREADS)
-k_dist(const __grid_constant__ Args a, const typename Store<P>::T* __restrict__ fs,
-       const typename Store<P>::T* __restrict__ gs, const double* __restrict__ hp,
+k_dist(const __grid_constant__ Args a, const TF<P>* __restrict__ fs,
+       const TG<P>* __restrict__ gs, const double* __restrict__ hp,
        double* __restrict__ Qf, double* __restrict__ Qg) {
     LBPC_NODE_XYZ
     dist_node<P, LAYOUT, FLOW>(a, x, y, z, fs, gs, hp, Qf, Qg);
@@ -1246,9 +1296,9 @@ k_dist(const __grid_constant__ Args a, const typename Store<P>::T* __restrict__ 
 // ---- adjoint kernels ----
 template <int P, bool FLOW>
 __global__ void __launch_bounds__(STEP_THREADS)
-k_step_tape(const __grid_constant__ Args a, const typename Store<P>::T* fs, typename Store<P>::T* fd,
-            const typename Store<P>::T* gs, typename Store<P>::T* gd, double* __restrict__ hp,
-            double* __restrict__ tape_e, typename Store<P>::C* __restrict__ tape_m) {
+k_step_tape(const __grid_constant__ Args a, const TF<P>* fs, TF<P>* fd,
+            const TG<P>* gs, TG<P>* gd, double* __restrict__ hp,
+            double* __restrict__ tape_e, CT<P>* __restrict__ tape_m) {
     LBPC_NODE_XYZ
     step_node<P, STEP_PULL, FLOW, true>(a, x, y, z, fs, fd, gs, gd, hp, tape_e, tape_m);
 }
@@ -1272,8 +1322,8 @@ __device__ __forceinline__ int block_linear() {
 
 template <int P, bool FLOW>
 __global__ void __launch_bounds__(STEP_THREADS)
-k_adj_seed(const __grid_constant__ Args a, const typename Store<P>::T* __restrict__ gs,
-           const double* __restrict__ hp, typename Store<P>::C* __restrict__ lam,
+k_adj_seed(const __grid_constant__ Args a, const TG<P>* __restrict__ gs,
+           const double* __restrict__ hp, CT<P>* __restrict__ lam,
            double* __restrict__ Lpart, double* __restrict__ Jpart) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -1291,9 +1341,9 @@ k_adj_seed(const __grid_constant__ Args a, const typename Store<P>::T* __restric
 
 template <int P, bool FLOW>
 __global__ void __launch_bounds__(STEP_THREADS)
-k_adj_reverse(const __grid_constant__ Args a, const typename Store<P>::C* __restrict__ lin,
-              typename Store<P>::C* __restrict__ lout, const double* __restrict__ tape_e,
-              const typename Store<P>::C* __restrict__ tape_m, int wface, double* gtw,
+k_adj_reverse(const __grid_constant__ Args a, const CT<P>* __restrict__ lin,
+              CT<P>* __restrict__ lout, const double* __restrict__ tape_e,
+              const CT<P>* __restrict__ tape_m, int wface, double* gtw,
               double* __restrict__ Lpart) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -1321,7 +1371,8 @@ inline dim3 node_grid(const Args& a, dim3 blk) {
 
 template <int P>
 struct Impl {
-    using T = typename Store<P>::T;
+    using T = TF<P>;
+    using TGp = TG<P>;
 
     template <int KIND, bool FLOW>
     static void step_k(const Args& a, const void* fs, void* fd, const void* gs, void* gd,
@@ -1330,12 +1381,12 @@ struct Impl {
             const int pairs = a.nx / 2;
             const dim3 blk = node_block_dims(pairs);
             const dim3 grd((pairs + blk.x - 1) / blk.x, (a.ny + blk.y - 1) / blk.y, a.nz);
-            k_step_pull_x2<P, FLOW><<<grd, blk, 0, s>>>(a, (const T*)fs, (T*)fd, (const T*)gs,
-                                                        (T*)gd, hp);
+            k_step_pull_x2<P, FLOW><<<grd, blk, 0, s>>>(a, (const T*)fs, (T*)fd, (const TGp*)gs,
+                                                        (TGp*)gd, hp);
             return;
         }
         const dim3 blk = node_block(a), grd = node_grid(a, blk);
-        k_step<P, KIND, FLOW><<<grd, blk, 0, s>>>(a, (const T*)fs, (T*)fd, (const T*)gs, (T*)gd, hp);
+        k_step<P, KIND, FLOW><<<grd, blk, 0, s>>>(a, (const T*)fs, (T*)fd, (const TGp*)gs, (TGp*)gd, hp);
     }
     static void step(const Args& a, StepKind kind, const void* fs, void* fd, const void* gs,
                      void* gd, double* hp, cudaStream_t s) {
@@ -1353,7 +1404,7 @@ struct Impl {
     template <int LAYOUT, bool FLOW>
     static void macro_k(const Args& a, const void* f, const void* g, const double* hp,
                         const MacroOut& o, cudaStream_t s) {
-        k_macro<P, LAYOUT, FLOW><<<RED_BLOCKS, RED_THREADS, 0, s>>>(a, (const T*)f, (const T*)g, hp, o);
+        k_macro<P, LAYOUT, FLOW><<<RED_BLOCKS, RED_THREADS, 0, s>>>(a, (const T*)f, (const TGp*)g, hp, o);
     }
     static void macro(const Args& a, Layout lay, const void* f, const void* g, const double* hp,
                       const MacroOut& o, cudaStream_t s) {
@@ -1372,13 +1423,13 @@ struct Impl {
                      const double* h0, void* f, void* g, double* hp, cudaStream_t s) {
         const dim3 blk = node_block(a), grd = node_grid(a, blk);
         if (lay == LAYOUT_PULL) {
-            if (a.flow) k_init<P, LAYOUT_PULL, true><<<grd, blk, 0, s>>>(a, Qf, Qg, h0, (T*)f, (T*)g);
-            else k_init<P, LAYOUT_PULL, false><<<grd, blk, 0, s>>>(a, Qf, Qg, h0, (T*)f, (T*)g);
-            k_init_hprime<P, LAYOUT_PULL><<<grd, blk, 0, s>>>(a, Qg, h0, (const T*)g, hp);
+            if (a.flow) k_init<P, LAYOUT_PULL, true><<<grd, blk, 0, s>>>(a, Qf, Qg, h0, (T*)f, (TGp*)g);
+            else k_init<P, LAYOUT_PULL, false><<<grd, blk, 0, s>>>(a, Qf, Qg, h0, (T*)f, (TGp*)g);
+            k_init_hprime<P, LAYOUT_PULL><<<grd, blk, 0, s>>>(a, Qg, h0, (const TGp*)g, hp);
         } else {
-            if (a.flow) k_init<P, LAYOUT_AA_NATURAL, true><<<grd, blk, 0, s>>>(a, Qf, Qg, h0, (T*)f, (T*)g);
-            else k_init<P, LAYOUT_AA_NATURAL, false><<<grd, blk, 0, s>>>(a, Qf, Qg, h0, (T*)f, (T*)g);
-            k_init_hprime<P, LAYOUT_AA_NATURAL><<<grd, blk, 0, s>>>(a, Qg, h0, (const T*)g, hp);
+            if (a.flow) k_init<P, LAYOUT_AA_NATURAL, true><<<grd, blk, 0, s>>>(a, Qf, Qg, h0, (T*)f, (TGp*)g);
+            else k_init<P, LAYOUT_AA_NATURAL, false><<<grd, blk, 0, s>>>(a, Qf, Qg, h0, (T*)f, (TGp*)g);
+            k_init_hprime<P, LAYOUT_AA_NATURAL><<<grd, blk, 0, s>>>(a, Qg, h0, (const TGp*)g, hp);
         }
     }
 
@@ -1386,8 +1437,8 @@ struct Impl {
     static void dist_k(const Args& a, const void* f, const void* g, const double* hp,
                        double* Qf, double* Qg, cudaStream_t s) {
         const dim3 blk = node_block(a), grd = node_grid(a, blk);
-        if (a.flow) k_dist<P, LAYOUT, true><<<grd, blk, 0, s>>>(a, (const T*)f, (const T*)g, hp, Qf, Qg);
-        else k_dist<P, LAYOUT, false><<<grd, blk, 0, s>>>(a, (const T*)f, (const T*)g, hp, Qf, Qg);
+        if (a.flow) k_dist<P, LAYOUT, true><<<grd, blk, 0, s>>>(a, (const T*)f, (const TGp*)g, hp, Qf, Qg);
+        else k_dist<P, LAYOUT, false><<<grd, blk, 0, s>>>(a, (const T*)f, (const TGp*)g, hp, Qf, Qg);
     }
     static void dist(const Args& a, Layout lay, const void* f, const void* g, const double* hp,
                      double* Qf, double* Qg, cudaStream_t s) {
@@ -1399,26 +1450,26 @@ struct Impl {
     static void step_tape(const Args& a, const void* fs, void* fd, const void* gs, void* gd,
                           double* hp, double* tape_e, void* tape_m, cudaStream_t s) {
         const dim3 blk = node_block(a), grd = node_grid(a, blk);
-        using C = typename Store<P>::C;
+        using C = CT<P>;
         if (a.flow)
-            k_step_tape<P, true><<<grd, blk, 0, s>>>(a, (const T*)fs, (T*)fd, (const T*)gs, (T*)gd,
+            k_step_tape<P, true><<<grd, blk, 0, s>>>(a, (const T*)fs, (T*)fd, (const TGp*)gs, (TGp*)gd,
                                                      hp, tape_e, (C*)tape_m);
         else
-            k_step_tape<P, false><<<grd, blk, 0, s>>>(a, (const T*)fs, (T*)fd, (const T*)gs, (T*)gd,
+            k_step_tape<P, false><<<grd, blk, 0, s>>>(a, (const T*)fs, (T*)fd, (const TGp*)gs, (TGp*)gd,
                                                       hp, tape_e, (C*)tape_m);
     }
     static void adj_seed(const Args& a, const void* gs, const double* hp, void* lam,
                          double* Lpart, double* Jpart, cudaStream_t s) {
         const dim3 blk = node_block(a), grd = node_grid(a, blk);
-        using C = typename Store<P>::C;
-        if (a.flow) k_adj_seed<P, true><<<grd, blk, 0, s>>>(a, (const T*)gs, hp, (C*)lam, Lpart, Jpart);
-        else k_adj_seed<P, false><<<grd, blk, 0, s>>>(a, (const T*)gs, hp, (C*)lam, Lpart, Jpart);
+        using C = CT<P>;
+        if (a.flow) k_adj_seed<P, true><<<grd, blk, 0, s>>>(a, (const TGp*)gs, hp, (C*)lam, Lpart, Jpart);
+        else k_adj_seed<P, false><<<grd, blk, 0, s>>>(a, (const TGp*)gs, hp, (C*)lam, Lpart, Jpart);
     }
     static void adj_reverse(const Args& a, const void* lin, void* lout, const double* tape_e,
                             const void* tape_m, int wface, double* gtw, double* Lpart,
                             cudaStream_t s) {
         const dim3 blk = node_block(a), grd = node_grid(a, blk);
-        using C = typename Store<P>::C;
+        using C = CT<P>;
         if (a.flow)
             k_adj_reverse<P, true><<<grd, blk, 0, s>>>(a, (const C*)lin, (C*)lout, tape_e,
                                                        (const C*)tape_m, wface, gtw, Lpart);
@@ -1429,7 +1480,7 @@ struct Impl {
 
     static const Launchers& table() {
         static const Launchers L = {&step, &macro, &init, &dist, &step_tape, &adj_seed,
-                                    &adj_reverse, sizeof(T), sizeof(typename Store<P>::C)};
+                                    &adj_reverse, sizeof(T), sizeof(TGp), sizeof(CT<P>)};
         return L;
     }
 };

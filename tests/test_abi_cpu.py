@@ -47,6 +47,8 @@ def test_param_block_layout_matches():
     (inp.FP16, inp.PULL, inp.FLOW_MRT, 2 * 25 * 2 + 16),
     (inp.BF16, inp.AA, inp.FLOW_MRT, 25 * 2 + 16),
     (inp.FP64, inp.PULL, inp.FLOW_NONE, 2 * 6 * 8 + 16),
+    (inp.FP16_G32, inp.PULL, inp.FLOW_MRT, 2 * (19 * 2 + 6 * 4) + 16),
+    (inp.BF16_G32, inp.AA, inp.FLOW_MRT, 19 * 2 + 6 * 4 + 16),
 ])
 def test_workspace_bytes_per_node(precision, streaming, flow, per_node):
     p = inp.Params(precision=precision, streaming=streaming, flow_model=flow, tau_g=0.8)
@@ -60,7 +62,7 @@ def test_workspace_bytes_per_node(precision, streaming, flow, per_node):
 
 
 @pytest.mark.parametrize("bad", [
-    dict(flow_model=7), dict(enth_model=0), dict(precision=9), dict(streaming=3),
+    dict(flow_model=7), dict(enth_model=0), dict(precision=6), dict(streaming=3),
     dict(bc=[0, 1, 2, 2, 2, 2]), dict(St=0.0), dict(omega_T=0.5), dict(Cp_s=-1.0),
     dict(Th=0.0), dict(tau_g=0.4), dict(Ra=-1.0), dict(Ma=2.0), dict(s_e=2.5),
     dict(sigma4=2.2), dict(report_every=-1),

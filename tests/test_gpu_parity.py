@@ -121,10 +121,12 @@ def test_wall_temperature_field_fp64():
 # ------------------------------------------------------------------------------------
 # One step from a random non-equilibrium state, every storage precision
 # ------------------------------------------------------------------------------------
-TOL = {inp.FP64: 1e-13, inp.FP32: 5e-6, inp.FP16: 2.5e-4, inp.BF16: 2e-3}
+TOL = {inp.FP64: 1e-13, inp.FP32: 5e-6, inp.FP16: 2.5e-4, inp.BF16: 2e-3, inp.FP16_G32: 2.5e-4,
+       inp.BF16_G32: 2e-3}
 
 
-@pytest.mark.parametrize("precision", [inp.FP64, inp.FP32, inp.FP16, inp.BF16])
+@pytest.mark.parametrize("precision", [inp.FP64, inp.FP32, inp.FP16, inp.BF16, inp.FP16_G32,
+                                       inp.BF16_G32])
 @pytest.mark.parametrize("streaming", [inp.PULL, inp.AA])
 @pytest.mark.parametrize("flow_model", [inp.FLOW_MRT, inp.FLOW_SRT, inp.FLOW_NONE])
 @pytest.mark.parametrize("nx", [19, 20])  # odd: one node per thread; even: node pairs
@@ -174,7 +176,8 @@ def test_aa_and_pull_agree(precision, tol):
         assert np.abs(res[inp.PULL][k] - res[inp.AA][k]).max() <= tol, k
 
 
-@pytest.mark.parametrize("precision,tol", [(inp.FP32, 1e-5), (inp.FP16, 1e-3), (inp.BF16, 1e-2)])
+@pytest.mark.parametrize("precision,tol", [(inp.FP32, 1e-5), (inp.FP16, 1e-3), (inp.BF16, 1e-2),
+                                           (inp.FP16_G32, 1e-4), (inp.BF16_G32, 1e-3)])
 def test_cavity_reduced_precision_tracks_oracle(precision, tol):
     shape = (24, 16, 12)
     p = inp.Params(precision=precision, Ra=1e5, Pr=0.71, St=1.0)
@@ -191,7 +194,8 @@ def test_cavity_reduced_precision_tracks_oracle(precision, tol):
 # Conservation, checkpoints, diagnostics history, divergence detection
 # ------------------------------------------------------------------------------------
 @pytest.mark.parametrize("precision,rho_tol", [(inp.FP64, 1e-13), (inp.FP32, 1e-5),
-                                               (inp.FP16, 2e-3), (inp.BF16, 2e-2)])
+                                               (inp.FP16, 2e-3), (inp.BF16, 2e-2),
+                                               (inp.FP16_G32, 2e-3), (inp.BF16_G32, 2e-2)])
 def test_closed_box_conserves_enthalpy_exactly(precision, rho_tol):
     """Adiabatic no-slip box with buoyancy and phase change: the FP64 rest channel makes
     sum h exact to FP64 rounding in every storage precision (Eq. 9 telescoping)."""
