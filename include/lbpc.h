@@ -199,10 +199,11 @@ lbpc_status lbpc_load(lbpc_handle *h, const void *host_buf, size_t bytes);
  * enters through L = C_p,l (Th - Tm) / St (Eq. 2, 64).  Derivatives at the kinks of the
  * Eq. 2 inversion are those of the branch the forward took.
  *
- * Memory stays bounded by checkpointing: the forward saves the state every ckpt_every
- * steps; the backward recomputes each segment writing a per-step macroscopic tape
+ * Memory stays bounded by checkpointing: the forward saves the state at the start of
+ * every ckpt_every-step segment but the last and writes the per-step macroscopic tape
  * (h - h_s in FP64, rho and j in the compute precision: 24 B per node and step in FP32)
- * and sweeps it backwards.  The adjoint populations are kept in the compute precision;
+ * over the last segment; the backward sweeps that tape backwards, then for each earlier
+ * segment recomputes it from its checkpoint writing the tape, and sweeps it backwards.  The adjoint populations are kept in the compute precision;
  * the parameter gradients accumulate in FP64.  Pull streaming only (LBPC_ERR_STATE
  * otherwise).  dev_ws: device, 256-byte aligned, >= lbpc_adjoint_workspace_bytes().
  *

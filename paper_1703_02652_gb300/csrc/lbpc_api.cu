@@ -712,16 +712,28 @@ lbpc_status lbpc_adjoint_forward(lbpc_handle* h, int nsteps, int ckpt_every, voi
     A.Lpart = (double*)(w + L.Lpart);
     A.Jpart = (double*)(w + L.Jpart);
     A.red = (double*)(w + L.red);
-    // forward with a checkpoint at the start of every segment and one of the final state
-    s = save_state(h, A.ckpt);
-    if (s != LBPC_OK) return s;
+    // Forward with a checkpoint at the start of every segment but the last, and one of the
+    // final state.  The last segment writes its tape as it goes, so the backward sweep
+    // starts on it without recomputing it (and needs no checkpoint at its start).
+    const int tail = (L.nseg - 1) * ckpt_every;
+    if (L.nseg > 1) {
+        s = save_state(h, A.ckpt);
+        if (s != LBPC_OK) return s;
+    }
     for (int i = 0; i < nsteps; i++) {
-        h->L->step(h->args, STEP_PULL, h->f[h->cur], h->f[1 - h->cur], h->g[h->cur], h->g[1 - h->cur],
-                   h->hp, h->stream);
+        if (i < tail) {
+            h->L->step(h->args, STEP_PULL, h->f[h->cur], h->f[1 - h->cur], h->g[h->cur],
+                       h->g[1 - h->cur], h->hp, h->stream);
+        } else {
+            const size_t t = (size_t)(i - tail);
+            h->L->step_tape(h->args, h->f[h->cur], h->f[1 - h->cur], h->g[h->cur], h->g[1 - h->cur],
+                            h->hp, A.tape_e + t * h->N,
+                            (char*)A.tape_m + t * 4 * h->N * h->L->compute_bytes, h->stream);
+        }
         h->cur = 1 - h->cur;
         h->step++;
         h->launches++;
-        if ((i + 1) % ckpt_every == 0 && i + 1 < nsteps) {
+        if ((i + 1) % ckpt_every == 0 && i + 1 < tail) {
             s = save_state(h, A.ckpt + (size_t)((i + 1) / ckpt_every) * A.ckpt_bytes);
             if (s != LBPC_OK) return s;
         }
@@ -755,20 +767,23 @@ lbpc_status lbpc_adjoint_backward(lbpc_handle* h, int face, double* dJ_dTw_host,
     int cl = 0;
     for (int seg = A.nseg - 1; seg >= 0; seg--) {
         const int start = seg * A.k, len = std::min(A.k, A.nsteps - start);
-        s = restore_state(h, A.ckpt + (size_t)seg * A.ckpt_bytes);
-        if (s != LBPC_OK) return s;
-        for (int t = 0; t < len; t++) {  // recompute the segment, writing the tape
-            h->L->step_tape(h->args, h->f[h->cur], h->f[1 - h->cur], h->g[h->cur], h->g[1 - h->cur],
-                            h->hp, A.tape_e + (size_t)t * N, (char*)A.tape_m + (size_t)t * 4 * N * Cb,
-                            h->stream);
-            h->cur = 1 - h->cur;
+        if (seg < A.nseg - 1) {  // the last segment's tape is the forward's
+            s = restore_state(h, A.ckpt + (size_t)seg * A.ckpt_bytes);
+            if (s != LBPC_OK) return s;
+            for (int t = 0; t < len; t++) {  // recompute the segment, writing the tape
+                h->L->step_tape(h->args, h->f[h->cur], h->f[1 - h->cur], h->g[h->cur],
+                                h->g[1 - h->cur], h->hp, A.tape_e + (size_t)t * N,
+                                (char*)A.tape_m + (size_t)t * 4 * N * Cb, h->stream);
+                h->cur = 1 - h->cur;
+            }
+            h->launches += len;
         }
         for (int t = len - 1; t >= 0; t--) {  // reverse sweep
             h->L->adj_reverse(h->args, A.lam[cl], A.lam[1 - cl], A.tape_e + (size_t)t * N,
                               (char*)A.tape_m + (size_t)t * 4 * N * Cb, face, A.gtw, A.Lpart, h->stream);
             cl = 1 - cl;
         }
-        h->launches += 2 * len;
+        h->launches += len;
     }
     k_sum<<<1, 256, 0, h->stream>>>(A.Lpart, A.nblocks, A.red + 1);
     h->launches++;

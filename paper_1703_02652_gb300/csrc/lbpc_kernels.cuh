@@ -670,14 +670,45 @@ LBPC_HD void step_node(const Args& a, int x, int y, int z, const TF<P>* fs,
 }
 
 
+// Inversion and both collisions of a node pair (n0, n0 + 1), in registers; with TAPE
+// also the macroscopic tape of the pair's pre-collision state (adjoint).
+template <int P, bool FLOW, bool TAPE = false>
+LBPC_HD void pair_collide(const Args& a, CT<P>* f0, CT<P>* f1, CT<P>* g0, CT<P>* g1, double e0,
+                          double e1, int n0 = 0, double* tape_e = nullptr,
+                          CT<P>* tape_m = nullptr) {
+    using C = CT<P>;
+    using VC = typename Vec2<C>::type;
+    const Coef<C>& k = coef<C>(a);
+    C T0, fl0, T1, fl1;
+    invert_excess(k, e0, T0, fl0);
+    invert_excess(k, e1, T1, fl1);
+    C ux0 = C(0), uy0 = C(0), uz0 = C(0), ux1 = C(0), uy1 = C(0), uz1 = C(0);
+    if constexpr (FLOW) {
+        C r0, jx0, jy0, jz0, r1, jx1, jy1, jz1;
+        collide_flow(f0, k, T0, fl0, ux0, uy0, uz0, r0, jx0, jy0, jz0);
+        collide_flow(f1, k, T1, fl1, ux1, uy1, uz1, r1, jx1, jy1, jz1);
+        if constexpr (TAPE) {
+            const size_t N = (size_t)a.N;
+            *reinterpret_cast<VC*>(tape_m + n0) = VC{r0, r1};
+            *reinterpret_cast<VC*>(tape_m + N + n0) = VC{jx0, jx1};
+            *reinterpret_cast<VC*>(tape_m + 2 * N + n0) = VC{jy0, jy1};
+            *reinterpret_cast<VC*>(tape_m + 3 * N + n0) = VC{jz0, jz1};
+        }
+    }
+    if constexpr (TAPE) *reinterpret_cast<double2*>(tape_e + n0) = make_double2(e0, e1);
+    collide_enth(g0, k, T0, fl0, ux0, uy0, uz0);
+    collide_enth(g1, k, T1, fl1, ux1, uy1, uz1);
+}
+
 // Two nodes (x0, x0 + 1), x0 even, of a row away from every y and z face: populations
 // with e_x = 0 move as aligned pairs; e_x = +-1 ones are two scalar loads, with the
 // x-face rules applied by selects on the lanes at x = 0 / x = nx - 1; every store is a
 // pair.  Requires even nx.
-template <int P, bool FLOW>
+template <int P, bool FLOW, bool TAPE = false>
 LBPC_HD void step_pair_pull(const Args& a, int x0, int y, int z, const TF<P>* fs,
                             TF<P>* fd, const TG<P>* gs,
-                            TG<P>* gd, double* hp) {
+                            TG<P>* gd, double* hp, double* tape_e = nullptr,
+                            CT<P>* tape_m = nullptr) {
     using SF = Store<Mode<P>::F>;
     using SG = Store<Mode<P>::G>;
     using TFt = typename SF::T;
@@ -744,21 +775,13 @@ LBPC_HD void step_pair_pull(const Args& a, int x0, int y, int z, const TF<P>* fs
 #undef LBPC_PG
     const double2 ep = ld_any<true>(reinterpret_cast<const double2*>(hp + n0));
     const double e0 = excess_plus<Mode<P>::G>(ep.x, g0), e1 = excess_plus<Mode<P>::G>(ep.y, g1);
-    C T0, fl0, T1, fl1;
-    invert_excess(k, e0, T0, fl0);
-    invert_excess(k, e1, T1, fl1);
-    C ux0 = C(0), uy0 = C(0), uz0 = C(0), ux1 = C(0), uy1 = C(0), uz1 = C(0);
+    pair_collide<P, FLOW, TAPE>(a, f0, f1, g0, g1, e0, e1, n0, tape_e, tape_m);
     if constexpr (FLOW) {
-        C r, jx, jy, jz;
-        collide_flow(f0, k, T0, fl0, ux0, uy0, uz0, r, jx, jy, jz);
-        collide_flow(f1, k, T1, fl1, ux1, uy1, uz1, r, jx, jy, jz);
 #define LBPC_SPF(q, ex, ey, ez, op)                                                      \
         *reinterpret_cast<VF*>(fd + (size_t)q * N + n0) = PRF::enc(f0[q], f1[q], fshift(k, q));
         LBPC_Q19(LBPC_SPF)
 #undef LBPC_SPF
     }
-    collide_enth(g0, k, T0, fl0, ux0, uy0, uz0);
-    collide_enth(g1, k, T1, fl1, ux1, uy1, uz1);
 #define LBPC_SPG(q, ex, ey, ez, op)                                                      \
     {                                                                                   \
         const VG v = PRG::enc_g(g0[q], g1[q], k.gshift);                                \
@@ -768,6 +791,176 @@ LBPC_HD void step_pair_pull(const Args& a, int x0, int y, int z, const TF<P>* fs
     LBPC_Q7(LBPC_SPG)
 #undef LBPC_SPG
     *reinterpret_cast<double2*>(hp + n0) = make_double2(excess_minus<Mode<P>::G>(e0, g0), excess_minus<Mode<P>::G>(e1, g1));
+}
+
+
+// Hides v's value from the compiler: the scatter addresses of the odd AA step equal gather
+// addresses, and without this the compiler keeps them all live across the collision.
+template <class T>
+LBPC_HD void opaque(T& v) {
+#if defined(__CUDA_ARCH__)
+    if constexpr (sizeof(T) == 8) asm volatile("" : "+l"(v));
+    else asm volatile("" : "+r"(v));
+#else
+    (void)v;
+#endif
+}
+
+// AA in-place streaming, two nodes (x0, x0 + 1) per thread, row away from the y/z faces.
+// Even step (natural layout): every access is a local aligned pair; f*_q goes to slot qbar.
+// Odd step (swapped layout): f_q(x) is slot qbar at x - e_q (slot q at x behind a wall) and
+// f*_q goes to slot q at x + e_q (slot qbar at x behind a wall), with the wall rules of the
+// per-node path.  Each thread reads and writes the same set of slots, so in place is safe.
+template <int P, bool FLOW, bool ODD>
+LBPC_HD void step_pair_aa(const Args& a, int x0, int y, int z, TF<P>* F, TG<P>* G, double* hp) {
+    using SF = Store<Mode<P>::F>;
+    using SG = Store<Mode<P>::G>;
+    using TFt = typename SF::T;
+    using TGt = typename SG::T;
+    using C = CT<P>;
+    using VF = typename Vec2<TFt>::type;
+    using VG = typename Vec2<TGt>::type;
+    using PRF = Pair<Mode<P>::F>;
+    using PRG = Pair<Mode<P>::G>;
+    const Coef<C>& k = coef<C>(a);
+    const size_t N = (size_t)a.N;
+    const int sy = a.nx, sz = a.nx * a.ny;
+    const int n0 = x0 + a.nx * (y + a.ny * z), n1 = n0 + 1;
+    const bool xlo = x0 == 0, xhi = x0 + 1 == a.nx - 1;
+    const bool wlo = xlo && a.wall[0], whi = xhi && a.wall[1];
+    const int dn0 = xlo ? n0 + a.nx - 1 : n0 - 1;      // x-neighbour x0 - 1 (wrapped)
+    const int up1 = xhi ? n1 - (a.nx - 1) : n1 + 1;    // x-neighbour x1 + 1 (wrapped)
+    C f0[19], f1[19], g0[7], g1[7];
+    // ---- gather ----
+    if constexpr (FLOW) {
+#define LBPC_AGF(q, ex, ey, ez, op)                                                      \
+        {                                                                               \
+            const C sh = fshift(k, q);                                                  \
+            if constexpr (!ODD) {                                                       \
+                PRF::dec(*reinterpret_cast<const VF*>(F + (size_t)q * N + n0), sh, f0[q], f1[q]); \
+            } else {                                                                    \
+                const int oyz = -(ey) * sy - (ez) * sz;                                 \
+                const TFt* sw = F + (size_t)op * N;                                     \
+                if constexpr ((ex) == 0) {                                              \
+                    PRF::dec(*reinterpret_cast<const VF*>(sw + n0 + oyz), sh, f0[q], f1[q]); \
+                } else if constexpr ((ex) == 1) {                                       \
+                    f0[q] = SF::dec(wlo ? F[(size_t)q * N + n0] : sw[dn0 + oyz], sh);  \
+                    f1[q] = SF::dec(sw[n0 + oyz], sh);                                \
+                } else {                                                                \
+                    f0[q] = SF::dec(sw[n1 + oyz], sh);                                \
+                    f1[q] = SF::dec(whi ? F[(size_t)q * N + n1] : sw[up1 + oyz], sh);  \
+                }                                                                       \
+            }                                                                           \
+        }
+        LBPC_Q19(LBPC_AGF)
+#undef LBPC_AGF
+    }
+#define LBPC_AGG(q, ex, ey, ez, op)                                                      \
+    {                                                                                   \
+        if constexpr (!ODD) {                                                           \
+            PRG::dec(*reinterpret_cast<const VG*>(G + (size_t)(q - 1) * N + n0), k.gshift, g0[q], g1[q]); \
+        } else {                                                                        \
+            const int oyz = -(ey) * sy - (ez) * sz;                                     \
+            const TGt* sw = G + (size_t)(op - 1) * N;                                   \
+            if constexpr ((ex) == 0) {                                                  \
+                PRG::dec(*reinterpret_cast<const VG*>(sw + n0 + oyz), k.gshift, g0[q], g1[q]); \
+            } else if constexpr ((ex) == 1) {                                           \
+                C v = SG::dec(wlo ? G[(size_t)(q - 1) * N + n0] : sw[dn0 + oyz], k.gshift);  \
+                if (wlo && a.wall_iso[0]) v = SG::grid(-v + abb_source(a, k, 0, x0, y, z)); \
+                g0[q] = v;                                                              \
+                g1[q] = SG::dec(sw[n0 + oyz], k.gshift);                                    \
+            } else {                                                                    \
+                g0[q] = SG::dec(sw[n1 + oyz], k.gshift);                                    \
+                C v = SG::dec(whi ? G[(size_t)(q - 1) * N + n1] : sw[up1 + oyz], k.gshift);  \
+                if (whi && a.wall_iso[1]) v = SG::grid(-v + abb_source(a, k, 1, x0 + 1, y, z)); \
+                g1[q] = v;                                                              \
+            }                                                                           \
+        }                                                                               \
+    }
+    LBPC_Q7(LBPC_AGG)
+#undef LBPC_AGG
+    const double2 ep = *reinterpret_cast<const double2*>(hp + n0);
+    const double e0 = excess_plus<Mode<P>::G>(ep.x, g0), e1 = excess_plus<Mode<P>::G>(ep.y, g1);
+    pair_collide<P, FLOW>(a, f0, f1, g0, g1, e0, e1);
+    // fresh copies of the indices and bases for the scatter (see opaque())
+    int m0 = n0, mdn = dn0, mup = up1, tsy = sy, tsz = sz;
+    TF<P>* Fw = F;
+    TG<P>* Gw = G;
+    if constexpr (ODD) {
+        opaque(m0); opaque(mdn); opaque(mup); opaque(tsy); opaque(tsz); opaque(Fw); opaque(Gw);
+    }
+    // ---- scatter ----
+    if constexpr (FLOW) {
+#define LBPC_ASF(q, ex, ey, ez, op)                                                      \
+        {                                                                               \
+            const C sh = fshift(k, q);                                                  \
+            if constexpr (!ODD) {                                                       \
+                *reinterpret_cast<VF*>(Fw + (size_t)op * N + m0) = PRF::enc(f0[q], f1[q], sh); \
+            } else {                                                                    \
+                const int o2 = (ey) * tsy + (ez) * tsz;                                   \
+                TFt* dq = Fw + (size_t)q * N;                                            \
+                if constexpr ((ex) == 0) {                                              \
+                    *reinterpret_cast<VF*>(dq + m0 + o2) = PRF::enc(f0[q], f1[q], sh);  \
+                } else if constexpr ((ex) == 1) {                                       \
+                    dq[(m0 + 1) + o2] = SF::enc(f0[q], sh);                                   \
+                    if (whi) Fw[(size_t)op * N + (m0 + 1)] = SF::enc(f1[q], sh);               \
+                    else dq[mup + o2] = SF::enc(f1[q], sh);                             \
+                } else {                                                                \
+                    if (wlo) Fw[(size_t)op * N + m0] = SF::enc(f0[q], sh);               \
+                    else dq[mdn + o2] = SF::enc(f0[q], sh);                             \
+                    dq[m0 + o2] = SF::enc(f1[q], sh);                                   \
+                }                                                                       \
+            }                                                                           \
+        }
+        LBPC_Q19(LBPC_ASF)
+#undef LBPC_ASF
+    }
+#define LBPC_ASG(q, ex, ey, ez, op)                                                      \
+    {                                                                                   \
+        if constexpr (!ODD) {                                                           \
+            const VG v = PRG::enc_g(g0[q], g1[q], k.gshift);                            \
+            *reinterpret_cast<VG*>(Gw + (size_t)(op - 1) * N + m0) = v;                   \
+            PRG::dec(v, k.gshift, g0[q], g1[q]);                                        \
+        } else {                                                                        \
+            const int o2 = (ey) * tsy + (ez) * tsz;                                       \
+            TGt* dq = Gw + (size_t)(q - 1) * N;                                          \
+            if constexpr ((ex) == 0) {                                                  \
+                const VG v = PRG::enc_g(g0[q], g1[q], k.gshift);                        \
+                *reinterpret_cast<VG*>(dq + m0 + o2) = v;                               \
+                PRG::dec(v, k.gshift, g0[q], g1[q]);                                    \
+            } else if constexpr ((ex) == 1) {                                           \
+                const TGt v0 = SG::enc_g(g0[q], k.gshift), v1 = SG::enc_g(g1[q], k.gshift); \
+                dq[(m0 + 1) + o2] = v0;                                                       \
+                if (whi) {                                                              \
+                    TGt vb = v1;                                                        \
+                    if (a.wall_iso[1])                                                  \
+                        vb = SG::enc_g(-SG::dec(v1, k.gshift) + abb_source(a, k, 1, x0 + 1, y, z), k.gshift); \
+                    Gw[(size_t)(op - 1) * N + (m0 + 1)] = vb;                                  \
+                } else {                                                                \
+                    dq[mup + o2] = v1;                                                  \
+                }                                                                       \
+                g0[q] = SG::dec(v0, k.gshift);                                          \
+                g1[q] = SG::dec(v1, k.gshift);                                          \
+            } else {                                                                    \
+                const TGt v0 = SG::enc_g(g0[q], k.gshift), v1 = SG::enc_g(g1[q], k.gshift); \
+                if (wlo) {                                                              \
+                    TGt vb = v0;                                                        \
+                    if (a.wall_iso[0])                                                  \
+                        vb = SG::enc_g(-SG::dec(v0, k.gshift) + abb_source(a, k, 0, x0, y, z), k.gshift); \
+                    Gw[(size_t)(op - 1) * N + m0] = vb;                                  \
+                } else {                                                                \
+                    dq[mdn + o2] = v0;                                                  \
+                }                                                                       \
+                dq[m0 + o2] = v1;                                                       \
+                g0[q] = SG::dec(v0, k.gshift);                                          \
+                g1[q] = SG::dec(v1, k.gshift);                                          \
+            }                                                                           \
+        }                                                                               \
+    }
+    LBPC_Q7(LBPC_ASG)
+#undef LBPC_ASG
+    *reinterpret_cast<double2*>(hp + n0) =
+        make_double2(excess_minus<Mode<P>::G>(e0, g0), excess_minus<Mode<P>::G>(e1, g1));
 }
 
 // Macroscopic state of node n and its contributions to the diagnostics sums
@@ -1233,6 +1426,27 @@ k_step_pull_x2(const __grid_constant__ Args a, const TF<P>* fs,
     }
 }
 
+
+// AA step, two nodes per thread along x (even nx); same vote as the pull pair kernel.
+template <int P, bool FLOW, bool ODD>
+__global__ void __launch_bounds__(STEP_THREADS, 4)
+k_step_aa_x2(const __grid_constant__ Args a, TF<P>* F, TG<P>* G, double* __restrict__ hp) {
+    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    const bool valid = x0 < a.nx && y < a.ny;
+    const bool inner = !valid || (y > 0 && y < a.ny - 1 && z > 0 && z < a.nz - 1);
+    const bool paired = __all_sync(0xffffffffu, inner);
+    if (!valid) return;
+    constexpr int KIND = ODD ? STEP_AA_ODD : STEP_AA_EVEN;
+    if (paired) {
+        step_pair_aa<P, FLOW, ODD>(a, x0, y, z, F, G, hp);
+    } else {
+        step_node<P, KIND, FLOW>(a, x0, y, z, F, F, G, G, hp);
+        step_node<P, KIND, FLOW>(a, x0 + 1, y, z, F, F, G, G, hp);
+    }
+}
+
 template <class T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
@@ -1301,6 +1515,28 @@ k_step_tape(const __grid_constant__ Args a, const TF<P>* fs, TF<P>* fd,
             double* __restrict__ tape_e, CT<P>* __restrict__ tape_m) {
     LBPC_NODE_XYZ
     step_node<P, STEP_PULL, FLOW, true>(a, x, y, z, fs, fd, gs, gd, hp, tape_e, tape_m);
+}
+
+// Pull step with the tape, two nodes per thread (even nx); the same pairing and vote as
+// k_step_pull_x2, so the state it produces is that of the plain step.
+template <int P, bool FLOW>
+__global__ void __launch_bounds__(STEP_THREADS)
+k_step_tape_x2(const __grid_constant__ Args a, const TF<P>* fs, TF<P>* fd,
+               const TG<P>* gs, TG<P>* gd, double* __restrict__ hp,
+               double* __restrict__ tape_e, CT<P>* __restrict__ tape_m) {
+    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    const bool valid = x0 < a.nx && y < a.ny;
+    const bool inner = !valid || (y > 0 && y < a.ny - 1 && z > 0 && z < a.nz - 1);
+    const bool paired = __all_sync(0xffffffffu, inner);
+    if (!valid) return;
+    if (paired) {
+        step_pair_pull<P, FLOW, true>(a, x0, y, z, fs, fd, gs, gd, hp, tape_e, tape_m);
+    } else {
+        step_node<P, STEP_PULL, FLOW, true>(a, x0, y, z, fs, fd, gs, gd, hp, tape_e, tape_m);
+        step_node<P, STEP_PULL, FLOW, true>(a, x0 + 1, y, z, fs, fd, gs, gd, hp, tape_e, tape_m);
+    }
 }
 
 // Sum of v over the block (STEP_THREADS threads), valid in thread 0.
@@ -1377,13 +1613,19 @@ struct Impl {
     template <int KIND, bool FLOW>
     static void step_k(const Args& a, const void* fs, void* fd, const void* gs, void* gd,
                        double* hp, cudaStream_t s) {
-        if (KIND == STEP_PULL && P != LBPC_FP64 && a.nx % 2 == 0) {
-            const int pairs = a.nx / 2;
-            const dim3 blk = node_block_dims(pairs);
-            const dim3 grd((pairs + blk.x - 1) / blk.x, (a.ny + blk.y - 1) / blk.y, a.nz);
-            k_step_pull_x2<P, FLOW><<<grd, blk, 0, s>>>(a, (const T*)fs, (T*)fd, (const TGp*)gs,
-                                                        (TGp*)gd, hp);
-            return;
+        if constexpr (P != LBPC_FP64) {  // FP64 keeps one node per thread
+            if (a.nx % 2 == 0) {
+                const int pairs = a.nx / 2;
+                const dim3 blk = node_block_dims(pairs);
+                const dim3 grd((pairs + blk.x - 1) / blk.x, (a.ny + blk.y - 1) / blk.y, a.nz);
+                if constexpr (KIND == STEP_PULL)
+                    k_step_pull_x2<P, FLOW><<<grd, blk, 0, s>>>(a, (const T*)fs, (T*)fd,
+                                                                (const TGp*)gs, (TGp*)gd, hp);
+                else
+                    k_step_aa_x2<P, FLOW, KIND == STEP_AA_ODD><<<grd, blk, 0, s>>>(a, (T*)fd,
+                                                                               (TGp*)gd, hp);
+                return;
+            }
         }
         const dim3 blk = node_block(a), grd = node_grid(a, blk);
         k_step<P, KIND, FLOW><<<grd, blk, 0, s>>>(a, (const T*)fs, (T*)fd, (const TGp*)gs, (TGp*)gd, hp);
@@ -1449,8 +1691,24 @@ struct Impl {
 
     static void step_tape(const Args& a, const void* fs, void* fd, const void* gs, void* gd,
                           double* hp, double* tape_e, void* tape_m, cudaStream_t s) {
-        const dim3 blk = node_block(a), grd = node_grid(a, blk);
         using C = CT<P>;
+        if constexpr (P != LBPC_FP64) {
+            if (a.nx % 2 == 0) {
+                const int pairs = a.nx / 2;
+                const dim3 blk = node_block_dims(pairs);
+                const dim3 grd((pairs + blk.x - 1) / blk.x, (a.ny + blk.y - 1) / blk.y, a.nz);
+                if (a.flow)
+                    k_step_tape_x2<P, true><<<grd, blk, 0, s>>>(a, (const T*)fs, (T*)fd,
+                                                               (const TGp*)gs, (TGp*)gd, hp, tape_e,
+                                                               (C*)tape_m);
+                else
+                    k_step_tape_x2<P, false><<<grd, blk, 0, s>>>(a, (const T*)fs, (T*)fd,
+                                                                (const TGp*)gs, (TGp*)gd, hp,
+                                                                tape_e, (C*)tape_m);
+                return;
+            }
+        }
+        const dim3 blk = node_block(a), grd = node_grid(a, blk);
         if (a.flow)
             k_step_tape<P, true><<<grd, blk, 0, s>>>(a, (const T*)fs, (T*)fd, (const TGp*)gs, (TGp*)gd,
                                                      hp, tape_e, (C*)tape_m);

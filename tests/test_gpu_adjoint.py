@@ -94,6 +94,37 @@ def test_fp32_gradients_track_fp64():
     assert abs(s32 - s64) <= 1e-3 * abs(s64)
 
 
+@pytest.mark.parametrize("precision", [inp.FP32, inp.FP16])
+def test_paired_tape_path(precision):
+    """A lattice wide enough (even nx, whole warps of interior rows) that the forward tail,
+    the segment recomputations and the plain steps run the two-nodes-per-thread kernels:
+    the gradient does not depend on the checkpoint interval, and tracks FP64."""
+    shape = (64, 8, 6)
+    ny, nz = shape[1], shape[2]
+    h0 = inp.h0_field(inp.cavity_melting(shape=shape))
+    Tw = inp.wall_temperature_field(ny, nz, seed=2)
+    res = {}
+    for prec, k in ((precision, 1), (precision, 8), (precision, 40), (inp.FP64, 40)):
+        p = inp.Params(precision=prec, Ra=1e5, Pr=6.2, St=1.0)
+        g = LBPC(shape, p)
+        g.set_wall_temperature(0, Tw)
+        g.set_initial_h(h0)
+        g.step(60)  # some melt first, so that the gradient is not zero
+        res[(prec, k)] = g.adjoint(40, k)
+    J1, g1, s1 = res[(precision, 1)]
+    for k in (8, 40):
+        J, gk, sk = res[(precision, k)]
+        assert abs(J - J1) <= 1e-9 * abs(J1)
+        assert np.abs(gk - g1).max() <= 1e-6 * np.abs(g1).max()
+        assert abs(sk - s1) <= 1e-6 * abs(s1)
+    J64, g64, s64 = res[(inp.FP64, 40)]
+    tol = 1e-3 if precision == inp.FP32 else 5e-2
+    print(precision, abs(J1 / J64 - 1), np.abs(g1 - g64).max() / np.abs(g64).max(), abs(s1 / s64 - 1))
+    assert abs(J1 - J64) <= (1e-4 if precision == inp.FP32 else 1e-3) * abs(J64)
+    assert np.abs(g1 - g64).max() <= tol * np.abs(g64).max()
+    assert abs(s1 - s64) <= tol * abs(s64)
+
+
 def test_autograd_function_matches_adjoint():
     shape, p, h0, Tw = _tiny(1, 1)
     T = torch.tensor(Tw, dtype=torch.float64, requires_grad=True)
