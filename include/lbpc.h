@@ -201,7 +201,7 @@ lbpc_status lbpc_load(lbpc_handle *h, const void *host_buf, size_t bytes);
  *
  * Memory stays bounded by checkpointing: the forward saves the state at the start of
  * every ckpt_every-step segment but the last and writes the per-step macroscopic tape
- * (h - h_s in FP64, rho and j in the compute precision: 24 B per node and step in FP32)
+ * (h - h_s, rho and j in the compute precision: 20 B per node and step in FP32)
  * over the last segment; the backward sweeps that tape backwards, then for each earlier
  * segment recomputes it from its checkpoint writing the tape, and sweeps it backwards.  The adjoint populations are kept in the compute precision;
  * the parameter gradients accumulate in FP64.  Pull streaming only (LBPC_ERR_STATE

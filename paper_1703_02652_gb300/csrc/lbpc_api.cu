@@ -158,7 +158,7 @@ struct lbpc_handle {
         long long end_step = 0;
         size_t ckpt_bytes = 0, off_f = 0, off_g = 0, off_hp = 0;
         char* ckpt = nullptr;
-        double* tape_e = nullptr;
+        void* tape_e = nullptr;
         void* tape_m = nullptr;
         void* lam[2] = {nullptr, nullptr};
         double *gtw = nullptr, *Lpart = nullptr, *Jpart = nullptr, *red = nullptr;
@@ -636,7 +636,7 @@ AdjLayout adj_layout(const lbpc_handle* h, int nsteps, int k) {
     L.ckpt_bytes = L.off_hp + align_up(8 * N);
     size_t off = 0;
     L.ckpt = off; off += (size_t)(L.nseg + 1) * L.ckpt_bytes;
-    L.tape_e = off; off = align_up(off + (size_t)k * 8 * N);
+    L.tape_e = off; off = align_up(off + (size_t)k * N * Cb);
     L.tape_m = off; off = align_up(off + (flow ? (size_t)k * 4 * N * Cb : 0));
     const size_t lam = (size_t)(flow ? 26 : 7) * N * Cb;
     L.lam0 = off; off = align_up(off + lam);
@@ -704,7 +704,7 @@ lbpc_status lbpc_adjoint_forward(lbpc_handle* h, int nsteps, int ckpt_every, voi
     A.ckpt_bytes = L.ckpt_bytes;
     A.off_f = L.off_f; A.off_g = L.off_g; A.off_hp = L.off_hp;
     A.ckpt = w + L.ckpt;
-    A.tape_e = (double*)(w + L.tape_e);
+    A.tape_e = w + L.tape_e;
     A.tape_m = w + L.tape_m;
     A.lam[0] = w + L.lam0;
     A.lam[1] = w + L.lam1;
@@ -727,7 +727,7 @@ lbpc_status lbpc_adjoint_forward(lbpc_handle* h, int nsteps, int ckpt_every, voi
         } else {
             const size_t t = (size_t)(i - tail);
             h->L->step_tape(h->args, h->f[h->cur], h->f[1 - h->cur], h->g[h->cur], h->g[1 - h->cur],
-                            h->hp, A.tape_e + t * h->N,
+                            h->hp, (char*)A.tape_e + t * h->N * h->L->compute_bytes,
                             (char*)A.tape_m + t * 4 * h->N * h->L->compute_bytes, h->stream);
         }
         h->cur = 1 - h->cur;
@@ -772,14 +772,14 @@ lbpc_status lbpc_adjoint_backward(lbpc_handle* h, int face, double* dJ_dTw_host,
             if (s != LBPC_OK) return s;
             for (int t = 0; t < len; t++) {  // recompute the segment, writing the tape
                 h->L->step_tape(h->args, h->f[h->cur], h->f[1 - h->cur], h->g[h->cur],
-                                h->g[1 - h->cur], h->hp, A.tape_e + (size_t)t * N,
+                                h->g[1 - h->cur], h->hp, (char*)A.tape_e + (size_t)t * N * Cb,
                                 (char*)A.tape_m + (size_t)t * 4 * N * Cb, h->stream);
                 h->cur = 1 - h->cur;
             }
             h->launches += len;
         }
         for (int t = len - 1; t >= 0; t--) {  // reverse sweep
-            h->L->adj_reverse(h->args, A.lam[cl], A.lam[1 - cl], A.tape_e + (size_t)t * N,
+            h->L->adj_reverse(h->args, A.lam[cl], A.lam[1 - cl], (char*)A.tape_e + (size_t)t * N * Cb,
                               (char*)A.tape_m + (size_t)t * 4 * N * Cb, face, A.gtw, A.Lpart, h->stream);
             cl = 1 - cl;
         }

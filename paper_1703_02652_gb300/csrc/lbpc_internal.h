@@ -68,10 +68,10 @@ struct Launchers {
     // adjoint: pull step that also writes the macroscopic tape (e: N doubles; rho, j:
     // 4N compute-precision values), seed of lambda at the final state, one reverse step
     void (*step_tape)(const Args&, const void* fs, void* fd, const void* gs, void* gd,
-                      double* hp, double* tape_e, void* tape_m, cudaStream_t);
+                      double* hp, void* tape_e, void* tape_m, cudaStream_t);
     void (*adj_seed)(const Args&, const void* gs, const double* hp, void* lam, double* Lpart,
                      double* Jpart, cudaStream_t);
-    void (*adj_reverse)(const Args&, const void* lin, void* lout, const double* tape_e,
+    void (*adj_reverse)(const Args&, const void* lin, void* lout, const void* tape_e,
                         const void* tape_m, int wface, double* gtw, double* Lpart, cudaStream_t);
     size_t f_bytes;        // bytes of one stored f value
     size_t g_bytes;        // bytes of one stored g value

@@ -624,7 +624,7 @@ template <> struct KindLayout<STEP_AA_ODD> { static constexpr int value = LAYOUT
 template <int P, int KIND, bool FLOW, bool TAPE = false>
 LBPC_HD void step_node(const Args& a, int x, int y, int z, const TF<P>* fs,
                        TF<P>* fd, const TG<P>* gs,
-                       TG<P>* gd, double* hp, double* tape_e = nullptr,
+                       TG<P>* gd, double* hp, CT<P>* tape_e = nullptr,
                        CT<P>* tape_m = nullptr) {
     using C = CT<P>;
     const Coef<C>& k = coef<C>(a);
@@ -649,8 +649,10 @@ LBPC_HD void step_node(const Args& a, int x, int y, int z, const TF<P>* fs,
     invert_excess(k, e, T, fl);
     C ux = C(0), uy = C(0), uz = C(0), rho = C(0), jx = C(0), jy = C(0), jz = C(0);
     if constexpr (FLOW) collide_flow(f, k, T, fl, ux, uy, uz, rho, jx, jy, jz);
-    if constexpr (TAPE) {  // macroscopic tape of the pre-collision state (adjoint)
-        tape_e[n] = e;
+    // macroscopic tape of the pre-collision state (adjoint), when asked for at run time: the
+    // plain and the taping step are one compiled kernel, so they agree to the last bit
+    if (TAPE && tape_e) {
+        tape_e[n] = to_compute(e, C(0));  // what the inversion uses
         if constexpr (FLOW) {
             tape_m[n] = rho;
             tape_m[(size_t)a.N + n] = jx;
@@ -670,11 +672,11 @@ LBPC_HD void step_node(const Args& a, int x, int y, int z, const TF<P>* fs,
 }
 
 
-// Inversion and both collisions of a node pair (n0, n0 + 1), in registers; with TAPE
-// also the macroscopic tape of the pair's pre-collision state (adjoint).
+// Inversion and both collisions of a node pair (n0, n0 + 1), in registers; with TAPE and a
+// non-null tape_e also the macroscopic tape of the pair's pre-collision state (adjoint).
 template <int P, bool FLOW, bool TAPE = false>
 LBPC_HD void pair_collide(const Args& a, CT<P>* f0, CT<P>* f1, CT<P>* g0, CT<P>* g1, double e0,
-                          double e1, int n0 = 0, double* tape_e = nullptr,
+                          double e1, int n0 = 0, CT<P>* tape_e = nullptr,
                           CT<P>* tape_m = nullptr) {
     using C = CT<P>;
     using VC = typename Vec2<C>::type;
@@ -687,7 +689,7 @@ LBPC_HD void pair_collide(const Args& a, CT<P>* f0, CT<P>* f1, CT<P>* g0, CT<P>*
         C r0, jx0, jy0, jz0, r1, jx1, jy1, jz1;
         collide_flow(f0, k, T0, fl0, ux0, uy0, uz0, r0, jx0, jy0, jz0);
         collide_flow(f1, k, T1, fl1, ux1, uy1, uz1, r1, jx1, jy1, jz1);
-        if constexpr (TAPE) {
+        if (TAPE && tape_e) {
             const size_t N = (size_t)a.N;
             *reinterpret_cast<VC*>(tape_m + n0) = VC{r0, r1};
             *reinterpret_cast<VC*>(tape_m + N + n0) = VC{jx0, jx1};
@@ -695,7 +697,8 @@ LBPC_HD void pair_collide(const Args& a, CT<P>* f0, CT<P>* f1, CT<P>* g0, CT<P>*
             *reinterpret_cast<VC*>(tape_m + 3 * N + n0) = VC{jz0, jz1};
         }
     }
-    if constexpr (TAPE) *reinterpret_cast<double2*>(tape_e + n0) = make_double2(e0, e1);
+    if (TAPE && tape_e)
+        *reinterpret_cast<VC*>(tape_e + n0) = VC{to_compute(e0, C(0)), to_compute(e1, C(0))};
     collide_enth(g0, k, T0, fl0, ux0, uy0, uz0);
     collide_enth(g1, k, T1, fl1, ux1, uy1, uz1);
 }
@@ -707,7 +710,7 @@ LBPC_HD void pair_collide(const Args& a, CT<P>* f0, CT<P>* f1, CT<P>* g0, CT<P>*
 template <int P, bool FLOW, bool TAPE = false>
 LBPC_HD void step_pair_pull(const Args& a, int x0, int y, int z, const TF<P>* fs,
                             TF<P>* fd, const TG<P>* gs,
-                            TG<P>* gd, double* hp, double* tape_e = nullptr,
+                            TG<P>* gd, double* hp, CT<P>* tape_e = nullptr,
                             CT<P>* tape_m = nullptr) {
     using SF = Store<Mode<P>::F>;
     using SG = Store<Mode<P>::G>;
@@ -1117,14 +1120,14 @@ LBPC_HD void dist_node(const Args& a, int x, int y, int z, const TF<P>* fs,
 // Adjoint (reverse mode) of one time step.  J = sum f_l(h_N); lambda is the adjoint of
 // the pre-collision populations, stored in the natural layout (f: 19 planes, g: 7 planes
 // including g_0).  The collision adjoint is evaluated from the macroscopic tape of the
-// pre-collision state (e = h - h_s, rho, j), which fixes every nonlinear factor.
+// pre-collision state (d = h - h_s rounded to the compute precision, exactly the value the
+// forward inversion used; rho, j), which fixes every nonlinear factor.
 // ---------------------------------------------------------------------------------
 
 // Derivatives of the Eq. 2 inversion on the branch the forward took.
 template <class C>
-LBPC_HD void invert_excess_d(const Coef<C>& k, double e, C& T, C& fl, C& dTde, C& dfde, C& dTdL,
+LBPC_HD void invert_excess_d(const Coef<C>& k, C d, C& T, C& fl, C& dTde, C& dfde, C& dTdL,
                              C& dfdL) {
-    const C d = to_compute(e, C(0));
     if (d <= C(0)) {
         fl = C(0); T = k.Tm + d * k.Cps_inv;
         dTde = k.Cps_inv; dfde = C(0); dTdL = C(0); dfdL = C(0);
@@ -1163,9 +1166,9 @@ LBPC_HD void enth_relax_op(const Coef<C>& k, const C* t, C* out) {
 // lf[19], lg[7]: in = adjoint of the post-collision populations, out = adjoint of the
 // pre-collision populations.  Returns the node's contribution to dJ/dL.
 template <class C, bool FLOW>
-LBPC_HD C collide_adjoint(const Coef<C>& k, double e, C rho, C jx, C jy, C jz, C* lf, C* lg) {
+LBPC_HD C collide_adjoint(const Coef<C>& k, C d, C rho, C jx, C jy, C jz, C* lf, C* lg) {
     C T, fl, dTde, dfde, dTdL, dfdL;
-    invert_excess_d(k, e, T, fl, dTde, dfde, dTdL, dfdL);
+    invert_excess_d(k, d, T, fl, dTde, dfde, dTdL, dfdL);
     C ux = C(0), uy = C(0), uz = C(0), usx = C(0), usy = C(0), usz = C(0), damp = C(0);
     C Fx = C(0), Fy = C(0), Fz = C(0);
     if constexpr (FLOW) {
@@ -1319,7 +1322,7 @@ LBPC_HD CT<P> adj_seed_node(const Args& a, int x, int y, int z,
     gather_g<Mode<P>::G, LAYOUT_PULL, true>(a, b, n, x, y, z, gs, g);
     const double e = excess_plus<Mode<P>::G>(hp[n], g);
     C T, fl, dTde, dfde, dTdL, dfdL;
-    invert_excess_d(k, e, T, fl, dTde, dfde, dTdL, dfdL);
+    invert_excess_d(k, to_compute(e, C(0)), T, fl, dTde, dfde, dTdL, dfdL);
     const size_t N = (size_t)a.N;
     const int nf = FLOW ? 19 : 0;
     for (int q = 0; q < nf; q++) lam[(size_t)q * N + n] = C(0);
@@ -1334,7 +1337,7 @@ LBPC_HD CT<P> adj_seed_node(const Args& a, int x, int y, int z,
 template <int P, bool FLOW, class NB>
 LBPC_HD CT<P> adj_reverse_node(const Args& a, const NB& b, int x, int y, int z,
                                               const CT<P>* lin,
-                                              CT<P>* lout, const double* tape_e,
+                                              CT<P>* lout, const CT<P>* tape_e,
                                               const CT<P>* tape_m, int wface,
                                               double* gtw) {
     using C = CT<P>;
@@ -1385,6 +1388,106 @@ LBPC_HD CT<P> adj_reverse_node(const Args& a, const NB& b, int x, int y, int z,
     return dL;
 }
 
+// Reverse step of two nodes (x0, x0 + 1) of a row away from every y and z face (even nx):
+// lambda_q of node x is lambda_{n+1} in plane q at x + e_q, or the reflected plane at x
+// when x + e_q lies behind an x wall; every other access is an aligned pair.
+template <int P, bool FLOW>
+LBPC_HD double adj_reverse_pair(const Args& a, int x0, int y, int z, const CT<P>* lin,
+                               CT<P>* lout, const CT<P>* tape_e, const CT<P>* tape_m,
+                               int wface, double* gtw) {
+    using C = CT<P>;
+    using VC = typename Vec2<C>::type;
+    const Coef<C>& k = coef<C>(a);
+    const size_t N = (size_t)a.N;
+    constexpr int nf = FLOW ? 19 : 0;
+    const int sy = a.nx, sz = a.nx * a.ny;
+    const int n0 = x0 + a.nx * (y + a.ny * z), n1 = n0 + 1;
+    const bool xlo = x0 == 0, xhi = x0 + 1 == a.nx - 1;
+    const bool wlo = xlo && a.wall[0], whi = xhi && a.wall[1];
+    const int dn0 = xlo ? n0 + a.nx - 1 : n0 - 1;    // x0 - 1 (wrapped)
+    const int up1 = xhi ? n1 - (a.nx - 1) : n1 + 1;  // x1 + 1 (wrapped)
+    C lf0[19], lf1[19], lg0[7], lg1[7];
+    if constexpr (FLOW) {
+#define LBPC_RF(q, ex, ey, ez, op)                                                       \
+        {                                                                               \
+            const int o = (ey) * sy + (ez) * sz;                                        \
+            const C* pl = lin + (size_t)q * N;                                          \
+            if constexpr ((ex) == 0) {                                                  \
+                const VC v = ld_any<true>(reinterpret_cast<const VC*>(pl + n0 + o));    \
+                lf0[q] = v.x; lf1[q] = v.y;                                             \
+            } else if constexpr ((ex) == 1) {                                           \
+                lf0[q] = ld_any<true>(pl + n1 + o);                                     \
+                lf1[q] = ld_any<true>(whi ? lin + (size_t)op * N + n1 : pl + up1 + o);  \
+            } else {                                                                    \
+                lf0[q] = ld_any<true>(wlo ? lin + (size_t)op * N + n0 : pl + dn0 + o);  \
+                lf1[q] = ld_any<true>(pl + n0 + o);                                     \
+            }                                                                           \
+        }
+        LBPC_Q19(LBPC_RF)
+#undef LBPC_RF
+    }
+    {
+        const VC v = ld_any<true>(reinterpret_cast<const VC*>(lin + (size_t)nf * N + n0));
+        lg0[0] = v.x; lg1[0] = v.y;
+    }
+#define LBPC_RG(q, ex, ey, ez, op)                                                       \
+    {                                                                                   \
+        const int o = (ey) * sy + (ez) * sz;                                            \
+        const C* pl = lin + (size_t)(nf + q) * N;                                       \
+        if constexpr ((ex) == 0) {                                                      \
+            const VC v = ld_any<true>(reinterpret_cast<const VC*>(pl + n0 + o));        \
+            lg0[q] = v.x; lg1[q] = v.y;                                                 \
+        } else if constexpr ((ex) == 1) {                                               \
+            lg0[q] = ld_any<true>(pl + n1 + o);                                         \
+            if (whi) {                                                                  \
+                const C la = ld_any<true>(lin + (size_t)(nf + op) * N + n1);            \
+                if (a.wall_iso[1]) {                                                    \
+                    lg1[q] = -la;                                                       \
+                    if (wface == 1) gtw[y + a.ny * z] += (double)k.wT_cref * (double)la; \
+                } else {                                                                \
+                    lg1[q] = la;                                                        \
+                }                                                                       \
+            } else {                                                                    \
+                lg1[q] = ld_any<true>(pl + up1 + o);                                    \
+            }                                                                           \
+        } else {                                                                        \
+            if (wlo) {                                                                  \
+                const C la = ld_any<true>(lin + (size_t)(nf + op) * N + n0);            \
+                if (a.wall_iso[0]) {                                                    \
+                    lg0[q] = -la;                                                       \
+                    if (wface == 0) gtw[y + a.ny * z] += (double)k.wT_cref * (double)la; \
+                } else {                                                                \
+                    lg0[q] = la;                                                        \
+                }                                                                       \
+            } else {                                                                    \
+                lg0[q] = ld_any<true>(pl + dn0 + o);                                    \
+            }                                                                           \
+            lg1[q] = ld_any<true>(pl + n0 + o);                                         \
+        }                                                                               \
+    }
+    LBPC_Q7(LBPC_RG)
+#undef LBPC_RG
+    C r0 = C(0), jx0 = C(0), jy0 = C(0), jz0 = C(0), r1 = C(0), jx1 = C(0), jy1 = C(0), jz1 = C(0);
+    if constexpr (FLOW) {
+        VC v = ld_any<true>(reinterpret_cast<const VC*>(tape_m + n0));
+        r0 = v.x; r1 = v.y;
+        v = ld_any<true>(reinterpret_cast<const VC*>(tape_m + N + n0));
+        jx0 = v.x; jx1 = v.y;
+        v = ld_any<true>(reinterpret_cast<const VC*>(tape_m + 2 * N + n0));
+        jy0 = v.x; jy1 = v.y;
+        v = ld_any<true>(reinterpret_cast<const VC*>(tape_m + 3 * N + n0));
+        jz0 = v.x; jz1 = v.y;
+    }
+    const VC d = ld_any<true>(reinterpret_cast<const VC*>(tape_e + n0));
+    const double dL = (double)collide_adjoint<C, FLOW>(k, d.x, r0, jx0, jy0, jz0, lf0, lg0) +
+                      (double)collide_adjoint<C, FLOW>(k, d.y, r1, jx1, jy1, jz1, lf1, lg1);
+    for (int q = 0; q < nf; q++)
+        *reinterpret_cast<VC*>(lout + (size_t)q * N + n0) = VC{lf0[q], lf1[q]};
+    for (int q = 0; q < 7; q++)
+        *reinterpret_cast<VC*>(lout + (size_t)(nf + q) * N + n0) = VC{lg0[q], lg1[q]};
+    return dL;
+}
+
 #if defined(__CUDACC__)
 // ---------------------------------------------------------------------------------
 // Kernels: one thread per node on a (x-block, y-block, z) grid.
@@ -1395,22 +1498,26 @@ LBPC_HD CT<P> adj_reverse_node(const Args& a, const NB& b, int x, int y, int z,
     const int z = blockIdx.z;                                                           \
     if (x >= a.nx || y >= a.ny) return;
 
+// One node per thread.  Pull steps write the adjoint tape when tape_e is not null.
 template <int P, int KIND, bool FLOW>
 __global__ void __launch_bounds__(STEP_THREADS)
 k_step(const __grid_constant__ Args a, const TF<P>* fs, TF<P>* fd,
-       const TG<P>* gs, TG<P>* gd, double* __restrict__ hp) {
+       const TG<P>* gs, TG<P>* gd, double* __restrict__ hp, CT<P>* __restrict__ tape_e,
+       CT<P>* __restrict__ tape_m) {
     LBPC_NODE_XYZ
-    step_node<P, KIND, FLOW>(a, x, y, z, fs, fd, gs, gd, hp);
+    step_node<P, KIND, FLOW, KIND == STEP_PULL>(a, x, y, z, fs, fd, gs, gd, hp, tape_e, tape_m);
 }
 
 
 // Pull step, two nodes per thread along x (even nx).  Warps whose rows all lie away
 // from the y and z faces take the paired path; others run the per-node path twice.
+// Writes the adjoint tape when tape_e is not null.
 template <int P, bool FLOW>
 __global__ void __launch_bounds__(STEP_THREADS)
 k_step_pull_x2(const __grid_constant__ Args a, const TF<P>* fs,
                TF<P>* fd, const TG<P>* gs, TG<P>* gd,
-               double* __restrict__ hp) {
+               double* __restrict__ hp, CT<P>* __restrict__ tape_e,
+               CT<P>* __restrict__ tape_m) {
     const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
@@ -1419,10 +1526,10 @@ k_step_pull_x2(const __grid_constant__ Args a, const TF<P>* fs,
     const bool paired = __all_sync(0xffffffffu, inner);
     if (!valid) return;
     if (paired) {
-        step_pair_pull<P, FLOW>(a, x0, y, z, fs, fd, gs, gd, hp);
+        step_pair_pull<P, FLOW, true>(a, x0, y, z, fs, fd, gs, gd, hp, tape_e, tape_m);
     } else {
-        step_node<P, STEP_PULL, FLOW>(a, x0, y, z, fs, fd, gs, gd, hp);
-        step_node<P, STEP_PULL, FLOW>(a, x0 + 1, y, z, fs, fd, gs, gd, hp);
+        step_node<P, STEP_PULL, FLOW, true>(a, x0, y, z, fs, fd, gs, gd, hp, tape_e, tape_m);
+        step_node<P, STEP_PULL, FLOW, true>(a, x0 + 1, y, z, fs, fd, gs, gd, hp, tape_e, tape_m);
     }
 }
 
@@ -1508,37 +1615,6 @@ k_dist(const __grid_constant__ Args a, const TF<P>* __restrict__ fs,
 
 
 // ---- adjoint kernels ----
-template <int P, bool FLOW>
-__global__ void __launch_bounds__(STEP_THREADS)
-k_step_tape(const __grid_constant__ Args a, const TF<P>* fs, TF<P>* fd,
-            const TG<P>* gs, TG<P>* gd, double* __restrict__ hp,
-            double* __restrict__ tape_e, CT<P>* __restrict__ tape_m) {
-    LBPC_NODE_XYZ
-    step_node<P, STEP_PULL, FLOW, true>(a, x, y, z, fs, fd, gs, gd, hp, tape_e, tape_m);
-}
-
-// Pull step with the tape, two nodes per thread (even nx); the same pairing and vote as
-// k_step_pull_x2, so the state it produces is that of the plain step.
-template <int P, bool FLOW>
-__global__ void __launch_bounds__(STEP_THREADS)
-k_step_tape_x2(const __grid_constant__ Args a, const TF<P>* fs, TF<P>* fd,
-               const TG<P>* gs, TG<P>* gd, double* __restrict__ hp,
-               double* __restrict__ tape_e, CT<P>* __restrict__ tape_m) {
-    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
-    const bool valid = x0 < a.nx && y < a.ny;
-    const bool inner = !valid || (y > 0 && y < a.ny - 1 && z > 0 && z < a.nz - 1);
-    const bool paired = __all_sync(0xffffffffu, inner);
-    if (!valid) return;
-    if (paired) {
-        step_pair_pull<P, FLOW, true>(a, x0, y, z, fs, fd, gs, gd, hp, tape_e, tape_m);
-    } else {
-        step_node<P, STEP_PULL, FLOW, true>(a, x0, y, z, fs, fd, gs, gd, hp, tape_e, tape_m);
-        step_node<P, STEP_PULL, FLOW, true>(a, x0 + 1, y, z, fs, fd, gs, gd, hp, tape_e, tape_m);
-    }
-}
-
 // Sum of v over the block (STEP_THREADS threads), valid in thread 0.
 __device__ __forceinline__ double block_sum(double v) {
     __shared__ double sh[STEP_THREADS / 32];
@@ -1578,7 +1654,7 @@ k_adj_seed(const __grid_constant__ Args a, const TG<P>* __restrict__ gs,
 template <int P, bool FLOW>
 __global__ void __launch_bounds__(STEP_THREADS)
 k_adj_reverse(const __grid_constant__ Args a, const CT<P>* __restrict__ lin,
-              CT<P>* __restrict__ lout, const double* __restrict__ tape_e,
+              CT<P>* __restrict__ lout, const CT<P>* __restrict__ tape_e,
               const CT<P>* __restrict__ tape_m, int wface, double* gtw,
               double* __restrict__ Lpart) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1597,6 +1673,33 @@ k_adj_reverse(const __grid_constant__ Args a, const CT<P>* __restrict__ lin,
     if (threadIdx.x == 0 && threadIdx.y == 0) Lpart[block_linear()] += s;
 }
 
+// Reverse step, two nodes per thread along x (even nx); the pull kernels' vote.
+template <int P, bool FLOW>
+__global__ void __launch_bounds__(STEP_THREADS, 4)
+k_adj_reverse_x2(const __grid_constant__ Args a, const CT<P>* __restrict__ lin,
+                 CT<P>* __restrict__ lout, const CT<P>* __restrict__ tape_e,
+                 const CT<P>* __restrict__ tape_m, int wface, double* gtw,
+                 double* __restrict__ Lpart) {
+    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    const bool valid = x0 < a.nx && y < a.ny;
+    const bool inner = !valid || (y > 0 && y < a.ny - 1 && z > 0 && z < a.nz - 1);
+    const bool paired = __all_sync(0xffffffffu, inner);
+    double dL = 0.0;
+    if (valid) {
+        if (paired) {
+            dL = adj_reverse_pair<P, FLOW>(a, x0, y, z, lin, lout, tape_e, tape_m, wface, gtw);
+        } else {
+            for (int x = x0; x < x0 + 2; x++)
+                dL += (double)adj_reverse_node<P, FLOW>(a, make_nb(a, x, y, z), x, y, z, lin, lout,
+                                                        tape_e, tape_m, wface, gtw);
+        }
+    }
+    const double s = block_sum(dL);
+    if (threadIdx.x == 0 && threadIdx.y == 0) Lpart[block_linear()] += s;
+}
+
 // ---------------------------------------------------------------------------------
 // Host launchers.
 // ---------------------------------------------------------------------------------
@@ -1610,9 +1713,12 @@ struct Impl {
     using T = TF<P>;
     using TGp = TG<P>;
 
+    // tape_e / tape_m: null, or (pull only) the adjoint tape of this step
     template <int KIND, bool FLOW>
     static void step_k(const Args& a, const void* fs, void* fd, const void* gs, void* gd,
-                       double* hp, cudaStream_t s) {
+                       double* hp, cudaStream_t s, void* tape_e = nullptr,
+                       void* tape_m = nullptr) {
+        using C = CT<P>;
         if constexpr (P != LBPC_FP64) {  // FP64 keeps one node per thread
             if (a.nx % 2 == 0) {
                 const int pairs = a.nx / 2;
@@ -1620,7 +1726,8 @@ struct Impl {
                 const dim3 grd((pairs + blk.x - 1) / blk.x, (a.ny + blk.y - 1) / blk.y, a.nz);
                 if constexpr (KIND == STEP_PULL)
                     k_step_pull_x2<P, FLOW><<<grd, blk, 0, s>>>(a, (const T*)fs, (T*)fd,
-                                                                (const TGp*)gs, (TGp*)gd, hp);
+                                                                (const TGp*)gs, (TGp*)gd, hp,
+                                                                (C*)tape_e, (C*)tape_m);
                 else
                     k_step_aa_x2<P, FLOW, KIND == STEP_AA_ODD><<<grd, blk, 0, s>>>(a, (T*)fd,
                                                                                (TGp*)gd, hp);
@@ -1628,7 +1735,8 @@ struct Impl {
             }
         }
         const dim3 blk = node_block(a), grd = node_grid(a, blk);
-        k_step<P, KIND, FLOW><<<grd, blk, 0, s>>>(a, (const T*)fs, (T*)fd, (const TGp*)gs, (TGp*)gd, hp);
+        k_step<P, KIND, FLOW><<<grd, blk, 0, s>>>(a, (const T*)fs, (T*)fd, (const TGp*)gs, (TGp*)gd, hp,
+                                                  (C*)tape_e, (C*)tape_m);
     }
     static void step(const Args& a, StepKind kind, const void* fs, void* fd, const void* gs,
                      void* gd, double* hp, cudaStream_t s) {
@@ -1689,32 +1797,11 @@ struct Impl {
         else dist_k<LAYOUT_AA_SWAPPED>(a, f, g, hp, Qf, Qg, s);
     }
 
+    // the pull step kernels themselves, with the tape pointers set
     static void step_tape(const Args& a, const void* fs, void* fd, const void* gs, void* gd,
-                          double* hp, double* tape_e, void* tape_m, cudaStream_t s) {
-        using C = CT<P>;
-        if constexpr (P != LBPC_FP64) {
-            if (a.nx % 2 == 0) {
-                const int pairs = a.nx / 2;
-                const dim3 blk = node_block_dims(pairs);
-                const dim3 grd((pairs + blk.x - 1) / blk.x, (a.ny + blk.y - 1) / blk.y, a.nz);
-                if (a.flow)
-                    k_step_tape_x2<P, true><<<grd, blk, 0, s>>>(a, (const T*)fs, (T*)fd,
-                                                               (const TGp*)gs, (TGp*)gd, hp, tape_e,
-                                                               (C*)tape_m);
-                else
-                    k_step_tape_x2<P, false><<<grd, blk, 0, s>>>(a, (const T*)fs, (T*)fd,
-                                                                (const TGp*)gs, (TGp*)gd, hp,
-                                                                tape_e, (C*)tape_m);
-                return;
-            }
-        }
-        const dim3 blk = node_block(a), grd = node_grid(a, blk);
-        if (a.flow)
-            k_step_tape<P, true><<<grd, blk, 0, s>>>(a, (const T*)fs, (T*)fd, (const TGp*)gs, (TGp*)gd,
-                                                     hp, tape_e, (C*)tape_m);
-        else
-            k_step_tape<P, false><<<grd, blk, 0, s>>>(a, (const T*)fs, (T*)fd, (const TGp*)gs, (TGp*)gd,
-                                                      hp, tape_e, (C*)tape_m);
+                          double* hp, void* tape_e, void* tape_m, cudaStream_t s) {
+        if (a.flow) step_k<STEP_PULL, true>(a, fs, fd, gs, gd, hp, s, tape_e, tape_m);
+        else step_k<STEP_PULL, false>(a, fs, fd, gs, gd, hp, s, tape_e, tape_m);
     }
     static void adj_seed(const Args& a, const void* gs, const double* hp, void* lam,
                          double* Lpart, double* Jpart, cudaStream_t s) {
@@ -1723,16 +1810,34 @@ struct Impl {
         if (a.flow) k_adj_seed<P, true><<<grd, blk, 0, s>>>(a, (const TGp*)gs, hp, (C*)lam, Lpart, Jpart);
         else k_adj_seed<P, false><<<grd, blk, 0, s>>>(a, (const TGp*)gs, hp, (C*)lam, Lpart, Jpart);
     }
-    static void adj_reverse(const Args& a, const void* lin, void* lout, const double* tape_e,
+    static void adj_reverse(const Args& a, const void* lin, void* lout, const void* tape_e,
                             const void* tape_m, int wface, double* gtw, double* Lpart,
                             cudaStream_t s) {
-        const dim3 blk = node_block(a), grd = node_grid(a, blk);
         using C = CT<P>;
+        if constexpr (P != LBPC_FP64) {
+            // the paired grid never has more blocks than the per-node one that sized Lpart
+            if (a.nx % 2 == 0) {
+                const int pairs = a.nx / 2;
+                const dim3 blk = node_block_dims(pairs);
+                const dim3 grd((pairs + blk.x - 1) / blk.x, (a.ny + blk.y - 1) / blk.y, a.nz);
+                if (a.flow)
+                    k_adj_reverse_x2<P, true><<<grd, blk, 0, s>>>(a, (const C*)lin, (C*)lout,
+                                                                 (const C*)tape_e, (const C*)tape_m,
+                                                                 wface, gtw, Lpart);
+                else
+                    k_adj_reverse_x2<P, false><<<grd, blk, 0, s>>>(a, (const C*)lin, (C*)lout,
+                                                                  (const C*)tape_e,
+                                                                  (const C*)tape_m, wface, gtw,
+                                                                  Lpart);
+                return;
+            }
+        }
+        const dim3 blk = node_block(a), grd = node_grid(a, blk);
         if (a.flow)
-            k_adj_reverse<P, true><<<grd, blk, 0, s>>>(a, (const C*)lin, (C*)lout, tape_e,
+            k_adj_reverse<P, true><<<grd, blk, 0, s>>>(a, (const C*)lin, (C*)lout, (const C*)tape_e,
                                                        (const C*)tape_m, wface, gtw, Lpart);
         else
-            k_adj_reverse<P, false><<<grd, blk, 0, s>>>(a, (const C*)lin, (C*)lout, tape_e,
+            k_adj_reverse<P, false><<<grd, blk, 0, s>>>(a, (const C*)lin, (C*)lout, (const C*)tape_e,
                                                         (const C*)tape_m, wface, gtw, Lpart);
     }
 
