@@ -110,10 +110,33 @@ inline void fill_coef(Coef<C>& c, const lbpc_params& p, const Derived& d) {
     c.fshift1 = (C)(shifted ? 1.0 / 18.0 : 0.0);
     c.fshift2 = (C)(shifted ? 1.0 / 36.0 : 0.0);
     c.gshift = (C)(gshifted ? 0.5 * p.omega_T * p.Cp_ref * p.Tref : 0.0);
-    // M applied to the rest weights (1/3, 1/18 x 6, 1/36 x 12): rows 0, 1, 2 (Eq. 51)
+    // row 0 of M (Eq. 51) applied to the rest weights (1/3, 1/18 x 6, 1/36 x 12)
     c.frho = (C)(shifted ? 1.0 : 0.0);
-    c.fm1 = (C)(shifted ? -11.0 : 0.0);
-    c.fm2 = (C)(shifted ? 3.0 : 0.0);
+    // Eq. 52-54 with the row norms |row k|^2 of Eq. 51 (2394, 252, 40, 36, 72, 12, 24, 4, 8);
+    // rows 1 and 2 carry the factor 19 of m1 - m1eq and the FF prefactors 38 and -11
+    c.r_e = (C)(-19.0 * d.s_e / 2394.0);
+    c.c_e = (C)(38.0 * (1.0 - 0.5 * d.s_e) / 2394.0);
+    c.r_eps = (C)(-d.s_eps / 252.0);
+    c.c_eps = (C)(-11.0 * (1.0 - 0.5 * d.s_eps) / 252.0);
+    c.r_q = (C)(-d.s_q / 40.0);
+    c.c_q = (C)(-(2.0 / 3.0) * (1.0 - 0.5 * d.s_q) / 40.0);
+    c.r_nu9 = (C)(-d.s_nu / 36.0);
+    c.c_nu9 = (C)((1.0 - 0.5 * d.s_nu) / 36.0);
+    c.r_pi10 = (C)(-d.s_pi / 72.0);
+    c.c_pi10 = (C)(-0.5 * (1.0 - 0.5 * d.s_pi) / 72.0);
+    c.r_nu11 = (C)(-d.s_nu / 12.0);
+    c.c_nu11 = (C)((1.0 - 0.5 * d.s_nu) / 12.0);
+    c.r_pi12 = (C)(-d.s_pi / 24.0);
+    c.c_pi12 = (C)(-0.5 * (1.0 - 0.5 * d.s_pi) / 24.0);
+    c.r_nu13 = (C)(-d.s_nu / 4.0);
+    c.c_nu13 = (C)((1.0 - 0.5 * d.s_nu) / 4.0);
+    c.r_t = (C)(-d.s_t / 8.0);
+    c.sig4_6 = (C)(d.sigma4 / 6.0);  // sig4 = sig5 = sig6 (Eq. 47)
+    c.sig5_6 = (C)(d.sigma4 / 6.0);
+    c.sig6_4 = (C)(d.sigma4 / 4.0);
+    c.hchi = (C)(0.5 * d.sigma_chi);
+    c.dCp = (C)(p.Cp_l - p.Cp_s);
+    c.gshift2 = (C)(gshifted ? p.omega_T * p.Cp_ref * p.Tref : 0.0);
 }
 
 // Kernel argument block of a validated parameter block; Tw[f] are the device (or host,

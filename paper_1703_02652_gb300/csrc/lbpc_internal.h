@@ -18,7 +18,14 @@ struct Coef {
     C s_e, s_eps, s_q, s_nu, s_pi, s_t;    // D3Q19 rates (Eq. 52)
     C fshift0, fshift1, fshift2;           // storage shifts of f: rest / axis / diagonal weight
     C gshift;                              // storage shift of g_1..6
-    C frho, fm1, fm2;  // moments 0, 1, 2 of the f shifts (1, -11, 3 when shifted, else 0)
+    C frho;  // moment 0 of the f shifts (1 when shifted, else 0); moments 1 and 2 (-11, 3)
+             // cancel against the rest-state equilibrium moments and need no constant
+    // D3Q19 relaxation with the row norms folded in: d_k = r_k (m_k - meq_k) + c_k FF_k,
+    // r_k = -s_k / |row k|^2, c_k = (1 - s_k / 2) (FF_k prefactor) / |row k|^2
+    C r_e, c_e, r_eps, c_eps, r_q, c_q, r_nu9, c_nu9, r_pi10, c_pi10, r_nu11, c_nu11, r_pi12,
+        c_pi12, r_nu13, c_nu13, r_t;
+    // D3Q7 relaxation: sig4 / 6, sig5 / 6, sig6 / 4, sig_chi / 2; Cp_l - Cp_s; 2 gshift
+    C sig4_6, sig5_6, sig6_4, hchi, dCp, gshift2;
 };
 
 struct Args {

@@ -443,22 +443,21 @@ LBPC_HD void collide_flow(C* f, const Coef<C>& k, C T, C fl, C& ux, C& uy, C& uz
     const C sax = a1 + a3 + a5, sdg = sxy + sxz + syz;
 
     const C rho = f[0] + sax + sdg + k.frho;
-    const C jx = b1 + xy_x + xz_x, jy = b3 + xy_y + yz_y, jz = b5 + xz_z + yz_z;
+    const C tx = xy_x + xz_x, ty = xy_y + yz_y, tz = xz_z + yz_z;
+    const C jx = b1 + tx, jy = b3 + ty, jz = b5 + tz;
     rho_o = rho;
     jx_o = jx;
     jy_o = jy;
     jz_o = jz;
-    // non-conserved moments (rows 1, 2, 4, 6, 8-18 of Eq. 51)
-    const C m1 = C(-30) * f[0] - C(11) * sax + C(8) * sdg + k.fm1;
-    const C m2 = C(12) * f[0] - C(4) * sax + sdg + k.fm2;
-    const C m4 = C(-4) * b1 + xy_x + xz_x;
-    const C m6 = C(-4) * b3 + xy_y + yz_y;
-    const C m8 = C(-4) * b5 + xz_z + yz_z;
-    const C m9 = C(2) * a1 - a3 - a5 + sxy + sxz - C(2) * syz;
-    const C m10 = C(-4) * a1 + C(2) * (a3 + a5) + sxy + sxz - C(2) * syz;
-    const C m11 = a3 - a5 + sxy - sxz;
-    const C m12 = C(2) * (a5 - a3) + sxy - sxz;
-    const C m13 = xy_p, m14 = yz_p, m15 = xz_p;
+    // non-conserved moments (rows 4, 6, 8-18 of Eq. 51); rows 1 and 2 enter below only as
+    // m1 - m1eq = 19 (sdg - f0 - rho u^2) and m2 - m2eq = 9 f0 - 7 sax - 2 sdg + 5.5 rho u^2,
+    // where the rest-weight constants of the stored representation cancel
+    const C m4 = tx - C(4) * b1, m6 = ty - C(4) * b3, m8 = tz - C(4) * b5;
+    const C a35 = a3 + a5, h9 = (sxy + sxz) - C(2) * syz;
+    const C m9 = C(2) * a1 - a35 + h9;
+    const C m10 = C(2) * a35 - C(4) * a1 + h9;
+    const C k11 = sxy - sxz, a53 = a5 - a3;
+    const C m11 = k11 - a53, m12 = C(2) * a53 + k11;
     const C m16 = xy_x - xz_x, m17 = yz_y - xy_y, m18 = xz_z - yz_z;
 
     // forces and velocity (Eq. 55-56 with the solid-phase force)
@@ -473,37 +472,35 @@ LBPC_HD void collide_flow(C* f, const Coef<C>& k, C T, C fl, C& ux, C& uy, C& uz
     // equilibrium moments (Eq. 53) and forcing moments (Eq. 54), c = 1
     const C uxx = ux * ux, uyy = uy * uy, uzz = uz * uz, u2 = uxx + uyy + uzz;
     const C Fu = Fx * ux + Fy * uy + Fz * uz;
+    const C ru2 = rho * u2, rux = rho * ux, r23 = C(2.0 / 3.0) * rho;
     const C pxx_eq = rho * (C(3) * uxx - u2), pww_eq = rho * (uyy - uzz);
     const C FFxx = C(6) * Fx * ux - C(2) * Fu, FFww = C(2) * (Fy * uy - Fz * uz);
-    const C c23 = C(2) / C(3);
 
-    // d_k = [-s_k (m_k - meq_k) + (1 - s_k/2) FF_k] / |row k|^2
-    const C he = C(1) - C(0.5) * k.s_e, hps = C(1) - C(0.5) * k.s_eps, hq = C(1) - C(0.5) * k.s_q;
-    const C hn = C(1) - C(0.5) * k.s_nu, hpi = C(1) - C(0.5) * k.s_pi;
-    const C d1 = (-k.s_e * (m1 - rho * (C(-11) + C(19) * u2)) + he * (C(38) * Fu)) * C(1.0 / 2394.0);
-    const C d2 = (-k.s_eps * (m2 - rho * (C(3) - C(5.5) * u2)) + hps * (C(-11) * Fu)) * C(1.0 / 252.0);
+    // d_k = [-s_k (m_k - meq_k) + (1 - s_k/2) FF_k] / |row k|^2; the products of the rates,
+    // (1 - s_k/2) and 1/|row k|^2 are folded into the r_* and c_* constants on the host
+    const C d1 = k.r_e * (sdg - f[0] - ru2) + k.c_e * Fu;
+    const C d2 = k.r_eps * (C(9) * f[0] - C(7) * sax - C(2) * sdg + C(5.5) * ru2) + k.c_eps * Fu;
     const C d3 = Fx * C(0.1), d5 = Fy * C(0.1), d7 = Fz * C(0.1);
-    const C d4 = (-k.s_q * (m4 + c23 * rho * ux) - hq * c23 * Fx) * C(1.0 / 40.0);
-    const C d6 = (-k.s_q * (m6 + c23 * rho * uy) - hq * c23 * Fy) * C(1.0 / 40.0);
-    const C d8 = (-k.s_q * (m8 + c23 * rho * uz) - hq * c23 * Fz) * C(1.0 / 40.0);
-    const C d9 = (-k.s_nu * (m9 - pxx_eq) + hn * FFxx) * C(1.0 / 36.0);
-    const C d10 = (-k.s_pi * (m10 + C(0.5) * pxx_eq) - hpi * C(0.5) * FFxx) * C(1.0 / 72.0);
-    const C d11 = (-k.s_nu * (m11 - pww_eq) + hn * FFww) * C(1.0 / 12.0);
-    const C d12 = (-k.s_pi * (m12 + C(0.5) * pww_eq) - hpi * C(0.5) * FFww) * C(1.0 / 24.0);
-    const C d13 = (-k.s_nu * (m13 - rho * ux * uy) + hn * (Fx * uy + Fy * ux)) * C(0.25);
-    const C d14 = (-k.s_nu * (m14 - rho * uy * uz) + hn * (Fy * uz + Fz * uy)) * C(0.25);
-    const C d15 = (-k.s_nu * (m15 - rho * ux * uz) + hn * (Fx * uz + Fz * ux)) * C(0.25);
-    const C d16 = -k.s_t * m16 * C(0.125);
-    const C d17 = -k.s_t * m17 * C(0.125);
-    const C d18 = -k.s_t * m18 * C(0.125);
+    const C d4 = k.r_q * (m4 + r23 * ux) + k.c_q * Fx;
+    const C d6 = k.r_q * (m6 + r23 * uy) + k.c_q * Fy;
+    const C d8 = k.r_q * (m8 + r23 * uz) + k.c_q * Fz;
+    const C d9 = k.r_nu9 * (m9 - pxx_eq) + k.c_nu9 * FFxx;
+    const C d10 = k.r_pi10 * (m10 + C(0.5) * pxx_eq) + k.c_pi10 * FFxx;
+    const C d11 = k.r_nu11 * (m11 - pww_eq) + k.c_nu11 * FFww;
+    const C d12 = k.r_pi12 * (m12 + C(0.5) * pww_eq) + k.c_pi12 * FFww;
+    const C d13 = k.r_nu13 * (xy_p - rux * uy) + k.c_nu13 * (Fx * uy + Fy * ux);
+    const C d14 = k.r_nu13 * (yz_p - rho * uy * uz) + k.c_nu13 * (Fy * uz + Fz * uy);
+    const C d15 = k.r_nu13 * (xz_p - rux * uz) + k.c_nu13 * (Fx * uz + Fz * ux);
+    const C d16 = k.r_t * m16, d17 = k.r_t * m17, d18 = k.r_t * m18;
 
-    // back-transform: f*_a = f_a + sum_k M_ka d_k (columns of Eq. 51)
+    // back-transform: f*_a = f_a + sum_k M_ka d_k (columns of Eq. 51), with the sums shared
+    // between the members of each axis pair and diagonal quadruple
     f[0] += C(-30) * d1 + C(12) * d2;
     const C eax = C(-11) * d1 - C(4) * d2;
     const C ox = d3 - C(4) * d4, oy = d5 - C(4) * d6, oz = d7 - C(4) * d8;
     const C ex1 = eax + C(2) * d9 - C(4) * d10;
-    const C ey1 = eax - d9 + C(2) * d10 + d11 - C(2) * d12;
-    const C ez1 = eax - d9 + C(2) * d10 - d11 + C(2) * d12;
+    const C cyz = eax - d9 + C(2) * d10, w11 = d11 - C(2) * d12;
+    const C ey1 = cyz + w11, ez1 = cyz - w11;
     f[1] += ex1 + ox;
     f[2] += ex1 - ox;
     f[3] += ey1 + oy;
@@ -512,54 +509,62 @@ LBPC_HD void collide_flow(C* f, const Coef<C>& k, C T, C fl, C& ux, C& uy, C& uz
     f[6] += ez1 - oz;
     const C edg = C(8) * d1 + d2;
     const C X = d3 + d4, Y = d5 + d6, Z = d7 + d8;
-    const C exy = edg + d9 + d10 + d11 + d12;
-    f[7] += exy + X + Y + d13 + d16 - d17;
-    f[8] += exy - X + Y - d13 - d16 - d17;
-    f[9] += exy + X - Y - d13 + d16 + d17;
-    f[10] += exy - X - Y + d13 - d16 + d17;
-    const C exz = edg + d9 + d10 - d11 - d12;
-    f[11] += exz + X + Z + d15 - d16 + d18;
-    f[12] += exz - X + Z - d15 + d16 + d18;
-    f[13] += exz + X - Z - d15 - d16 - d18;
-    f[14] += exz - X - Z + d15 + d16 - d18;
+    const C a910 = edg + d9 + d10, b1112 = d11 + d12;
+    const C exy = a910 + b1112, exz = a910 - b1112;
     const C eyz = edg - C(2) * d9 - C(2) * d10;
-    f[15] += eyz + Y + Z + d14 + d17 - d18;
-    f[16] += eyz - Y + Z - d14 - d17 - d18;
-    f[17] += eyz + Y - Z - d14 + d17 + d18;
-    f[18] += eyz - Y - Z + d14 - d17 + d18;
+    {  // xy: f7..f10 = e_xy +-(d13) + (+-X +-Y) + (+-d16 -+d17)
+        const C u = X + d16, v = Y - d17, P = exy + d13, Q = exy - d13;
+        const C s = u + v, w = v - u;
+        f[7] += P + s;
+        f[8] += Q + w;
+        f[9] += Q - w;
+        f[10] += P - s;
+    }
+    {  // xz: f11..f14
+        const C u = X - d16, v = Z + d18, P = exz + d15, Q = exz - d15;
+        const C s = u + v, w = v - u;
+        f[11] += P + s;
+        f[12] += Q + w;
+        f[13] += Q - w;
+        f[14] += P - s;
+    }
+    {  // yz: f15..f18
+        const C u = Y + d17, v = Z - d18, P = eyz + d14, Q = eyz - d14;
+        const C s = u + v, w = v - u;
+        f[15] += P + s;
+        f[16] += Q + w;
+        f[17] += Q - w;
+        f[18] += P - s;
+    }
 }
 
 // D3Q7 enthalpy collision on the six moving populations (Eq. 21-25; SRT when every
 // rate equals 1/tau_g).  With d_a = g_a - g_a^eq, d_0 = -sum d_a (h is conserved), the
 // moments of d are m1..m3 (odd pairs), m4 = -7 S, m5, m6; g* = g^eq + d - N^-1 R N d.
 template <class C>
-LBPC_HD void collide_enth(C* g, const Coef<C>& k, C T, C fl, C ux, C uy,
-                                             C uz) {
-    const C Cp = fl * k.Cpl + (C(1) - fl) * k.Cps;
-    const C cT = k.wa_cref * T - k.gshift;  // even part of g^eq_a (Eq. 7), representation
-    const C vT = C(0.5) * Cp * T;     // (omega_a / c_sT^2) Cp T = Cp T / 2
-    const C e1 = cT + vT * ux, e2 = cT - vT * ux;
-    const C e3 = cT + vT * uy, e4 = cT - vT * uy;
-    const C e5 = cT + vT * uz, e6 = cT - vT * uz;
-    const C d1 = g[1] - e1, d2 = g[2] - e2, d3 = g[3] - e3, d4 = g[4] - e4, d5 = g[5] - e5,
-            d6 = g[6] - e6;
-    const C m1 = d1 - d2, m2 = d3 - d4, m3 = d5 - d6;
-    const C p12 = d1 + d2, p34 = d3 + d4, p56 = d5 + d6;
-    const C S = p12 + p34 + p56;
-    const C m5 = C(2) * p12 - (p34 + p56);
-    const C m6 = p34 - p56;
-    const C A = k.sig4 * S * C(1.0 / 6.0);
-    const C B = k.sig5 * m5;
-    const C D = k.sig6 * m6 * C(0.25);
-    const C hc = C(0.5) * k.sig_chi;
-    const C c12 = A + B * C(1.0 / 6.0);
-    const C c36 = A - B * C(1.0 / 12.0);
-    g[1] = e1 + d1 - (hc * m1 + c12);
-    g[2] = e2 + d2 - (-hc * m1 + c12);
-    g[3] = e3 + d3 - (hc * m2 + c36 + D);
-    g[4] = e4 + d4 - (-hc * m2 + c36 + D);
-    g[5] = e5 + d5 - (hc * m3 + c36 - D);
-    g[6] = e6 + d6 - (-hc * m3 + c36 - D);
+LBPC_HD void collide_enth(C* g, const Coef<C>& k, C T, C fl, C ux, C uy, C uz) {
+    const C Cp = k.Cps + fl * k.dCp;
+    // an axis pair's equilibria (Eq. 7) sum to cT2 (representation) and differ by vT2 u
+    const C cT2 = k.wT_cref * T - k.gshift2;
+    const C vT2 = Cp * T;
+    // moments of d = g - g^eq: odd pair differences m1..m3, pair sums p
+    const C m1 = (g[1] - g[2]) - vT2 * ux;
+    const C m2 = (g[3] - g[4]) - vT2 * uy;
+    const C m3 = (g[5] - g[6]) - vT2 * uz;
+    const C p12 = (g[1] + g[2]) - cT2, p34 = (g[3] + g[4]) - cT2, p56 = (g[5] + g[6]) - cT2;
+    const C q = p34 + p56;
+    const C S = p12 + q, m5 = C(2) * p12 - q, m6 = p34 - p56;
+    // g* = g^eq + d - N^-1 R N d = g - N^-1 R N d, rates and 1/|row|^2 folded on the host
+    const C A = k.sig4_6 * S, B = k.sig5_6 * m5, D = k.sig6_4 * m6;
+    const C c12 = A + B, c36 = A - C(0.5) * B;
+    const C c3p = c36 + D, c3m = c36 - D;
+    const C h1 = k.hchi * m1, h2 = k.hchi * m2, h3 = k.hchi * m3;
+    g[1] -= c12 + h1;
+    g[2] -= c12 - h1;
+    g[3] -= c3p + h2;
+    g[4] -= c3p - h2;
+    g[5] -= c3m + h3;
+    g[6] -= c3m - h3;
 }
 
 // The rest channel stores e' = h' - h_s in FP64, so that e = h - h_s = e' + sum_{a>=1} g_a.
