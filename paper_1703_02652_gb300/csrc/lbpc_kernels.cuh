@@ -618,6 +618,8 @@ LBPC_HD double excess_minus(double e, const typename Store<P>::C* g) {
 // Node-level operations (host + device: the kernels below call them once per node).
 // ---------------------------------------------------------------------------------
 constexpr int STEP_THREADS = 128;
+// Largest lattice the pair paths take: they form plane offsets of up to 3 N in int.
+constexpr int kPairMaxN = 715827882;  // floor((2^31 - 1) / 3)
 
 template <int KIND> struct KindLayout;
 template <> struct KindLayout<STEP_PULL> { static constexpr int value = LAYOUT_PULL; };
@@ -654,9 +656,7 @@ LBPC_HD void step_node(const Args& a, int x, int y, int z, const TF<P>* fs,
     invert_excess(k, e, T, fl);
     C ux = C(0), uy = C(0), uz = C(0), rho = C(0), jx = C(0), jy = C(0), jz = C(0);
     if constexpr (FLOW) collide_flow(f, k, T, fl, ux, uy, uz, rho, jx, jy, jz);
-    // macroscopic tape of the pre-collision state (adjoint), when asked for at run time: the
-    // plain and the taping step are one compiled kernel, so they agree to the last bit
-    if (TAPE && tape_e) {
+    if constexpr (TAPE) {  // macroscopic tape of the pre-collision state (adjoint)
         tape_e[n] = to_compute(e, C(0));  // what the inversion uses
         if constexpr (FLOW) {
             tape_m[n] = rho;
@@ -677,8 +677,8 @@ LBPC_HD void step_node(const Args& a, int x, int y, int z, const TF<P>* fs,
 }
 
 
-// Inversion and both collisions of a node pair (n0, n0 + 1), in registers; with TAPE and a
-// non-null tape_e also the macroscopic tape of the pair's pre-collision state (adjoint).
+// Inversion and both collisions of a node pair (n0, n0 + 1), in registers; with TAPE also
+// the macroscopic tape of the pair's pre-collision state (adjoint).
 template <int P, bool FLOW, bool TAPE = false>
 LBPC_HD void pair_collide(const Args& a, CT<P>* f0, CT<P>* f1, CT<P>* g0, CT<P>* g1, double e0,
                           double e1, int n0 = 0, CT<P>* tape_e = nullptr,
@@ -694,7 +694,7 @@ LBPC_HD void pair_collide(const Args& a, CT<P>* f0, CT<P>* f1, CT<P>* g0, CT<P>*
         C r0, jx0, jy0, jz0, r1, jx1, jy1, jz1;
         collide_flow(f0, k, T0, fl0, ux0, uy0, uz0, r0, jx0, jy0, jz0);
         collide_flow(f1, k, T1, fl1, ux1, uy1, uz1, r1, jx1, jy1, jz1);
-        if (TAPE && tape_e) {
+        if constexpr (TAPE) {
             const size_t N = (size_t)a.N;
             *reinterpret_cast<VC*>(tape_m + n0) = VC{r0, r1};
             *reinterpret_cast<VC*>(tape_m + N + n0) = VC{jx0, jx1};
@@ -702,16 +702,17 @@ LBPC_HD void pair_collide(const Args& a, CT<P>* f0, CT<P>* f1, CT<P>* g0, CT<P>*
             *reinterpret_cast<VC*>(tape_m + 3 * N + n0) = VC{jz0, jz1};
         }
     }
-    if (TAPE && tape_e)
+    if constexpr (TAPE)
         *reinterpret_cast<VC*>(tape_e + n0) = VC{to_compute(e0, C(0)), to_compute(e1, C(0))};
     collide_enth(g0, k, T0, fl0, ux0, uy0, uz0);
     collide_enth(g1, k, T1, fl1, ux1, uy1, uz1);
 }
 
 // Two nodes (x0, x0 + 1), x0 even, of a row away from every y and z face: populations
-// with e_x = 0 move as aligned pairs; e_x = +-1 ones are two scalar loads, with the
-// x-face rules applied by selects on the lanes at x = 0 / x = nx - 1; every store is a
-// pair.  Requires even nx.
+// with e_x = 0 move as aligned pairs; e_x = +-1 ones are two scalar loads, with the x-face
+// rules (periodic wrap; at a wall the reflected population of the node itself) applied
+// by selecting a 32-bit element offset from the population's plane on the lanes at x = 0
+// / x = nx - 1; every store is a pair.  Requires even nx.
 template <int P, bool FLOW, bool TAPE = false>
 LBPC_HD void step_pair_pull(const Args& a, int x0, int y, int z, const TF<P>* fs,
                             TF<P>* fd, const TG<P>* gs,
@@ -728,6 +729,7 @@ LBPC_HD void step_pair_pull(const Args& a, int x0, int y, int z, const TF<P>* fs
     using PRG = Pair<Mode<P>::G>;
     const Coef<C>& k = coef<C>(a);
     const size_t N = (size_t)a.N;
+    const int N32 = a.N;  // 3 N < 2^31 (kPairMaxN)
     const int sy = a.nx, sz = a.nx * a.ny;
     const int n0 = x0 + a.nx * (y + a.ny * z), n1 = n0 + 1;
     const bool xlo = x0 == 0, xhi = x0 + 1 == a.nx - 1;
@@ -746,13 +748,13 @@ LBPC_HD void step_pair_pull(const Args& a, int x0, int y, int z, const TF<P>* fs
                 PRF::dec(ld_any<true>(reinterpret_cast<const VF*>(pl + n0 + oyz)),             \
                         sh, f0[q], f1[q]);                                              \
             } else if constexpr ((ex) == 1) {                                           \
-                const TFt* p0 = wlo ? fs + (size_t)op * N + n0 : pl + up0 + oyz;          \
-                f0[q] = SF::dec(ldv<Mode<P>::F, LAYOUT_PULL, true>(p0), sh);                      \
+                const int i0 = wlo ? ((op) - (q)) * N32 + n0 : up0 + oyz;               \
+                f0[q] = SF::dec(ldv<Mode<P>::F, LAYOUT_PULL, true>(pl + i0), sh);                 \
                 f1[q] = SF::dec(ldv<Mode<P>::F, LAYOUT_PULL, true>(pl + n0 + oyz), sh);           \
             } else {                                                                    \
-                const TFt* p1 = whi ? fs + (size_t)op * N + n1 : pl + up1 + oyz;          \
+                const int i1 = whi ? ((op) - (q)) * N32 + n1 : up1 + oyz;               \
                 f0[q] = SF::dec(ldv<Mode<P>::F, LAYOUT_PULL, true>(pl + n1 + oyz), sh);           \
-                f1[q] = SF::dec(ldv<Mode<P>::F, LAYOUT_PULL, true>(p1), sh);                      \
+                f1[q] = SF::dec(ldv<Mode<P>::F, LAYOUT_PULL, true>(pl + i1), sh);                 \
             }                                                                           \
         }
         LBPC_Q19(LBPC_PF)
@@ -766,14 +768,14 @@ LBPC_HD void step_pair_pull(const Args& a, int x0, int y, int z, const TF<P>* fs
             PRG::dec(ld_any<true>(reinterpret_cast<const VG*>(pl + n0 + oyz)),                 \
                     k.gshift, g0[q], g1[q]);                                            \
         } else if constexpr ((ex) == 1) {                                               \
-            const TGt* p0 = wlo ? gs + (size_t)(op - 1) * N + n0 : pl + up0 + oyz;        \
-            C v = SG::dec(ldv<Mode<P>::G, LAYOUT_PULL, true>(p0), k.gshift);                      \
+            const int i0 = wlo ? ((op) - (q)) * N32 + n0 : up0 + oyz;                   \
+            C v = SG::dec(ldv<Mode<P>::G, LAYOUT_PULL, true>(pl + i0), k.gshift);                 \
             if (wlo && a.wall_iso[0]) v = SG::grid(-v + abb_source(a, k, 0, x0, y, z)); \
             g0[q] = v;                                                                  \
             g1[q] = SG::dec(ldv<Mode<P>::G, LAYOUT_PULL, true>(pl + n0 + oyz), k.gshift);         \
         } else {                                                                        \
-            const TGt* p1 = whi ? gs + (size_t)(op - 1) * N + n1 : pl + up1 + oyz;        \
-            C v = SG::dec(ldv<Mode<P>::G, LAYOUT_PULL, true>(p1), k.gshift);                      \
+            const int i1 = whi ? ((op) - (q)) * N32 + n1 : up1 + oyz;                   \
+            C v = SG::dec(ldv<Mode<P>::G, LAYOUT_PULL, true>(pl + i1), k.gshift);                 \
             if (whi && a.wall_iso[1]) v = SG::grid(-v + abb_source(a, k, 1, x0 + 1, y, z)); \
             g1[q] = v;                                                                  \
             g0[q] = SG::dec(ldv<Mode<P>::G, LAYOUT_PULL, true>(pl + n1 + oyz), k.gshift);         \
@@ -832,6 +834,7 @@ LBPC_HD void step_pair_aa(const Args& a, int x0, int y, int z, TF<P>* F, TG<P>* 
     using PRG = Pair<Mode<P>::G>;
     const Coef<C>& k = coef<C>(a);
     const size_t N = (size_t)a.N;
+    const int N32 = a.N;  // 3 N < 2^31 (kPairMaxN)
     const int sy = a.nx, sz = a.nx * a.ny;
     const int n0 = x0 + a.nx * (y + a.ny * z), n1 = n0 + 1;
     const bool xlo = x0 == 0, xhi = x0 + 1 == a.nx - 1;
@@ -852,11 +855,11 @@ LBPC_HD void step_pair_aa(const Args& a, int x0, int y, int z, TF<P>* F, TG<P>* 
                 if constexpr ((ex) == 0) {                                              \
                     PRF::dec(*reinterpret_cast<const VF*>(sw + n0 + oyz), sh, f0[q], f1[q]); \
                 } else if constexpr ((ex) == 1) {                                       \
-                    f0[q] = SF::dec(wlo ? F[(size_t)q * N + n0] : sw[dn0 + oyz], sh);  \
+                    f0[q] = SF::dec(sw[wlo ? ((q) - (op)) * N32 + n0 : dn0 + oyz], sh);  \
                     f1[q] = SF::dec(sw[n0 + oyz], sh);                                \
                 } else {                                                                \
                     f0[q] = SF::dec(sw[n1 + oyz], sh);                                \
-                    f1[q] = SF::dec(whi ? F[(size_t)q * N + n1] : sw[up1 + oyz], sh);  \
+                    f1[q] = SF::dec(sw[whi ? ((q) - (op)) * N32 + n1 : up1 + oyz], sh);  \
                 }                                                                       \
             }                                                                           \
         }
@@ -873,13 +876,13 @@ LBPC_HD void step_pair_aa(const Args& a, int x0, int y, int z, TF<P>* F, TG<P>* 
             if constexpr ((ex) == 0) {                                                  \
                 PRG::dec(*reinterpret_cast<const VG*>(sw + n0 + oyz), k.gshift, g0[q], g1[q]); \
             } else if constexpr ((ex) == 1) {                                           \
-                C v = SG::dec(wlo ? G[(size_t)(q - 1) * N + n0] : sw[dn0 + oyz], k.gshift);  \
+                C v = SG::dec(sw[wlo ? ((q) - (op)) * N32 + n0 : dn0 + oyz], k.gshift);  \
                 if (wlo && a.wall_iso[0]) v = SG::grid(-v + abb_source(a, k, 0, x0, y, z)); \
                 g0[q] = v;                                                              \
                 g1[q] = SG::dec(sw[n0 + oyz], k.gshift);                                    \
             } else {                                                                    \
                 g0[q] = SG::dec(sw[n1 + oyz], k.gshift);                                    \
-                C v = SG::dec(whi ? G[(size_t)(q - 1) * N + n1] : sw[up1 + oyz], k.gshift);  \
+                C v = SG::dec(sw[whi ? ((q) - (op)) * N32 + n1 : up1 + oyz], k.gshift);  \
                 if (whi && a.wall_iso[1]) v = SG::grid(-v + abb_source(a, k, 1, x0 + 1, y, z)); \
                 g1[q] = v;                                                              \
             }                                                                           \
@@ -910,12 +913,10 @@ LBPC_HD void step_pair_aa(const Args& a, int x0, int y, int z, TF<P>* F, TG<P>* 
                 if constexpr ((ex) == 0) {                                              \
                     *reinterpret_cast<VF*>(dq + m0 + o2) = PRF::enc(f0[q], f1[q], sh);  \
                 } else if constexpr ((ex) == 1) {                                       \
-                    dq[(m0 + 1) + o2] = SF::enc(f0[q], sh);                                   \
-                    if (whi) Fw[(size_t)op * N + (m0 + 1)] = SF::enc(f1[q], sh);               \
-                    else dq[mup + o2] = SF::enc(f1[q], sh);                             \
+                    dq[(m0 + 1) + o2] = SF::enc(f0[q], sh);                             \
+                    dq[whi ? ((op) - (q)) * N32 + (m0 + 1) : mup + o2] = SF::enc(f1[q], sh); \
                 } else {                                                                \
-                    if (wlo) Fw[(size_t)op * N + m0] = SF::enc(f0[q], sh);               \
-                    else dq[mdn + o2] = SF::enc(f0[q], sh);                             \
+                    dq[wlo ? ((op) - (q)) * N32 + m0 : mdn + o2] = SF::enc(f0[q], sh);  \
                     dq[m0 + o2] = SF::enc(f1[q], sh);                                   \
                 }                                                                       \
             }                                                                           \
@@ -938,27 +939,19 @@ LBPC_HD void step_pair_aa(const Args& a, int x0, int y, int z, TF<P>* F, TG<P>* 
                 PRG::dec(v, k.gshift, g0[q], g1[q]);                                    \
             } else if constexpr ((ex) == 1) {                                           \
                 const TGt v0 = SG::enc_g(g0[q], k.gshift), v1 = SG::enc_g(g1[q], k.gshift); \
-                dq[(m0 + 1) + o2] = v0;                                                       \
-                if (whi) {                                                              \
-                    TGt vb = v1;                                                        \
-                    if (a.wall_iso[1])                                                  \
-                        vb = SG::enc_g(-SG::dec(v1, k.gshift) + abb_source(a, k, 1, x0 + 1, y, z), k.gshift); \
-                    Gw[(size_t)(op - 1) * N + (m0 + 1)] = vb;                                  \
-                } else {                                                                \
-                    dq[mup + o2] = v1;                                                  \
-                }                                                                       \
+                dq[(m0 + 1) + o2] = v0;                                                 \
+                TGt vb = v1;                                                            \
+                if (whi && a.wall_iso[1])                                               \
+                    vb = SG::enc_g(-SG::dec(v1, k.gshift) + abb_source(a, k, 1, x0 + 1, y, z), k.gshift); \
+                dq[whi ? ((op) - (q)) * N32 + (m0 + 1) : mup + o2] = vb;                \
                 g0[q] = SG::dec(v0, k.gshift);                                          \
                 g1[q] = SG::dec(v1, k.gshift);                                          \
             } else {                                                                    \
                 const TGt v0 = SG::enc_g(g0[q], k.gshift), v1 = SG::enc_g(g1[q], k.gshift); \
-                if (wlo) {                                                              \
-                    TGt vb = v0;                                                        \
-                    if (a.wall_iso[0])                                                  \
-                        vb = SG::enc_g(-SG::dec(v0, k.gshift) + abb_source(a, k, 0, x0, y, z), k.gshift); \
-                    Gw[(size_t)(op - 1) * N + m0] = vb;                                  \
-                } else {                                                                \
-                    dq[mdn + o2] = v0;                                                  \
-                }                                                                       \
+                TGt vb = v0;                                                            \
+                if (wlo && a.wall_iso[0])                                               \
+                    vb = SG::enc_g(-SG::dec(v0, k.gshift) + abb_source(a, k, 0, x0, y, z), k.gshift); \
+                dq[wlo ? ((op) - (q)) * N32 + m0 : mdn + o2] = vb;                      \
                 dq[m0 + o2] = v1;                                                       \
                 g0[q] = SG::dec(v0, k.gshift);                                          \
                 g1[q] = SG::dec(v1, k.gshift);                                          \
@@ -1404,6 +1397,7 @@ LBPC_HD double adj_reverse_pair(const Args& a, int x0, int y, int z, const CT<P>
     using VC = typename Vec2<C>::type;
     const Coef<C>& k = coef<C>(a);
     const size_t N = (size_t)a.N;
+    const int N32 = a.N;  // 3 N < 2^31 (kPairMaxN)
     constexpr int nf = FLOW ? 19 : 0;
     const int sy = a.nx, sz = a.nx * a.ny;
     const int n0 = x0 + a.nx * (y + a.ny * z), n1 = n0 + 1;
@@ -1422,9 +1416,9 @@ LBPC_HD double adj_reverse_pair(const Args& a, int x0, int y, int z, const CT<P>
                 lf0[q] = v.x; lf1[q] = v.y;                                             \
             } else if constexpr ((ex) == 1) {                                           \
                 lf0[q] = ld_any<true>(pl + n1 + o);                                     \
-                lf1[q] = ld_any<true>(whi ? lin + (size_t)op * N + n1 : pl + up1 + o);  \
+                lf1[q] = ld_any<true>(pl + (whi ? ((op) - (q)) * N32 + n1 : up1 + o)); \
             } else {                                                                    \
-                lf0[q] = ld_any<true>(wlo ? lin + (size_t)op * N + n0 : pl + dn0 + o);  \
+                lf0[q] = ld_any<true>(pl + (wlo ? ((op) - (q)) * N32 + n0 : dn0 + o)); \
                 lf1[q] = ld_any<true>(pl + n0 + o);                                     \
             }                                                                           \
         }
@@ -1444,29 +1438,15 @@ LBPC_HD double adj_reverse_pair(const Args& a, int x0, int y, int z, const CT<P>
             lg0[q] = v.x; lg1[q] = v.y;                                                 \
         } else if constexpr ((ex) == 1) {                                               \
             lg0[q] = ld_any<true>(pl + n1 + o);                                         \
-            if (whi) {                                                                  \
-                const C la = ld_any<true>(lin + (size_t)(nf + op) * N + n1);            \
-                if (a.wall_iso[1]) {                                                    \
-                    lg1[q] = -la;                                                       \
-                    if (wface == 1) gtw[y + a.ny * z] += (double)k.wT_cref * (double)la; \
-                } else {                                                                \
-                    lg1[q] = la;                                                        \
-                }                                                                       \
-            } else {                                                                    \
-                lg1[q] = ld_any<true>(pl + up1 + o);                                    \
-            }                                                                           \
+            const C la = ld_any<true>(pl + (whi ? ((op) - (q)) * N32 + n1 : up1 + o));  \
+            const bool iso = whi && a.wall_iso[1];                                      \
+            lg1[q] = iso ? -la : la;                                                    \
+            if (iso && wface == 1) gtw[y + a.ny * z] += (double)k.wT_cref * (double)la; \
         } else {                                                                        \
-            if (wlo) {                                                                  \
-                const C la = ld_any<true>(lin + (size_t)(nf + op) * N + n0);            \
-                if (a.wall_iso[0]) {                                                    \
-                    lg0[q] = -la;                                                       \
-                    if (wface == 0) gtw[y + a.ny * z] += (double)k.wT_cref * (double)la; \
-                } else {                                                                \
-                    lg0[q] = la;                                                        \
-                }                                                                       \
-            } else {                                                                    \
-                lg0[q] = ld_any<true>(pl + dn0 + o);                                    \
-            }                                                                           \
+            const C la = ld_any<true>(pl + (wlo ? ((op) - (q)) * N32 + n0 : dn0 + o));  \
+            const bool iso = wlo && a.wall_iso[0];                                      \
+            lg0[q] = iso ? -la : la;                                                    \
+            if (iso && wface == 0) gtw[y + a.ny * z] += (double)k.wT_cref * (double)la; \
             lg1[q] = ld_any<true>(pl + n0 + o);                                         \
         }                                                                               \
     }
@@ -1503,22 +1483,22 @@ LBPC_HD double adj_reverse_pair(const Args& a, int x0, int y, int z, const CT<P>
     const int z = blockIdx.z;                                                           \
     if (x >= a.nx || y >= a.ny) return;
 
-// One node per thread.  Pull steps write the adjoint tape when tape_e is not null.
-template <int P, int KIND, bool FLOW>
+// One node per thread; with TAPE (pull) also the adjoint tape.
+template <int P, int KIND, bool FLOW, bool TAPE>
 __global__ void __launch_bounds__(STEP_THREADS)
 k_step(const __grid_constant__ Args a, const TF<P>* fs, TF<P>* fd,
        const TG<P>* gs, TG<P>* gd, double* __restrict__ hp, CT<P>* __restrict__ tape_e,
        CT<P>* __restrict__ tape_m) {
     LBPC_NODE_XYZ
-    step_node<P, KIND, FLOW, KIND == STEP_PULL>(a, x, y, z, fs, fd, gs, gd, hp, tape_e, tape_m);
+    step_node<P, KIND, FLOW, TAPE>(a, x, y, z, fs, fd, gs, gd, hp, tape_e, tape_m);
 }
 
 
 // Pull step, two nodes per thread along x (even nx).  Warps whose rows all lie away
 // from the y and z faces take the paired path; others run the per-node path twice.
-// Writes the adjoint tape when tape_e is not null.
-template <int P, bool FLOW>
-__global__ void __launch_bounds__(STEP_THREADS)
+// With TAPE also the adjoint tape.  Five blocks per SM (96 registers); four when taping.
+template <int P, bool FLOW, bool TAPE>
+__global__ void __launch_bounds__(STEP_THREADS, TAPE ? 4 : 5)
 k_step_pull_x2(const __grid_constant__ Args a, const TF<P>* fs,
                TF<P>* fd, const TG<P>* gs, TG<P>* gd,
                double* __restrict__ hp, CT<P>* __restrict__ tape_e,
@@ -1531,10 +1511,10 @@ k_step_pull_x2(const __grid_constant__ Args a, const TF<P>* fs,
     const bool paired = __all_sync(0xffffffffu, inner);
     if (!valid) return;
     if (paired) {
-        step_pair_pull<P, FLOW, true>(a, x0, y, z, fs, fd, gs, gd, hp, tape_e, tape_m);
+        step_pair_pull<P, FLOW, TAPE>(a, x0, y, z, fs, fd, gs, gd, hp, tape_e, tape_m);
     } else {
-        step_node<P, STEP_PULL, FLOW, true>(a, x0, y, z, fs, fd, gs, gd, hp, tape_e, tape_m);
-        step_node<P, STEP_PULL, FLOW, true>(a, x0 + 1, y, z, fs, fd, gs, gd, hp, tape_e, tape_m);
+        step_node<P, STEP_PULL, FLOW, TAPE>(a, x0, y, z, fs, fd, gs, gd, hp, tape_e, tape_m);
+        step_node<P, STEP_PULL, FLOW, TAPE>(a, x0 + 1, y, z, fs, fd, gs, gd, hp, tape_e, tape_m);
     }
 }
 
@@ -1718,19 +1698,19 @@ struct Impl {
     using T = TF<P>;
     using TGp = TG<P>;
 
-    // tape_e / tape_m: null, or (pull only) the adjoint tape of this step
-    template <int KIND, bool FLOW>
+    // TAPE (pull only): also write the adjoint tape of this step to tape_e / tape_m
+    template <int KIND, bool FLOW, bool TAPE = false>
     static void step_k(const Args& a, const void* fs, void* fd, const void* gs, void* gd,
                        double* hp, cudaStream_t s, void* tape_e = nullptr,
                        void* tape_m = nullptr) {
         using C = CT<P>;
         if constexpr (P != LBPC_FP64) {  // FP64 keeps one node per thread
-            if (a.nx % 2 == 0) {
+            if (a.nx % 2 == 0 && a.N <= kPairMaxN) {
                 const int pairs = a.nx / 2;
                 const dim3 blk = node_block_dims(pairs);
                 const dim3 grd((pairs + blk.x - 1) / blk.x, (a.ny + blk.y - 1) / blk.y, a.nz);
                 if constexpr (KIND == STEP_PULL)
-                    k_step_pull_x2<P, FLOW><<<grd, blk, 0, s>>>(a, (const T*)fs, (T*)fd,
+                    k_step_pull_x2<P, FLOW, TAPE><<<grd, blk, 0, s>>>(a, (const T*)fs, (T*)fd,
                                                                 (const TGp*)gs, (TGp*)gd, hp,
                                                                 (C*)tape_e, (C*)tape_m);
                 else
@@ -1740,7 +1720,7 @@ struct Impl {
             }
         }
         const dim3 blk = node_block(a), grd = node_grid(a, blk);
-        k_step<P, KIND, FLOW><<<grd, blk, 0, s>>>(a, (const T*)fs, (T*)fd, (const TGp*)gs, (TGp*)gd, hp,
+        k_step<P, KIND, FLOW, TAPE><<<grd, blk, 0, s>>>(a, (const T*)fs, (T*)fd, (const TGp*)gs, (TGp*)gd, hp,
                                                   (C*)tape_e, (C*)tape_m);
     }
     static void step(const Args& a, StepKind kind, const void* fs, void* fd, const void* gs,
@@ -1802,11 +1782,10 @@ struct Impl {
         else dist_k<LAYOUT_AA_SWAPPED>(a, f, g, hp, Qf, Qg, s);
     }
 
-    // the pull step kernels themselves, with the tape pointers set
     static void step_tape(const Args& a, const void* fs, void* fd, const void* gs, void* gd,
                           double* hp, void* tape_e, void* tape_m, cudaStream_t s) {
-        if (a.flow) step_k<STEP_PULL, true>(a, fs, fd, gs, gd, hp, s, tape_e, tape_m);
-        else step_k<STEP_PULL, false>(a, fs, fd, gs, gd, hp, s, tape_e, tape_m);
+        if (a.flow) step_k<STEP_PULL, true, true>(a, fs, fd, gs, gd, hp, s, tape_e, tape_m);
+        else step_k<STEP_PULL, false, true>(a, fs, fd, gs, gd, hp, s, tape_e, tape_m);
     }
     static void adj_seed(const Args& a, const void* gs, const double* hp, void* lam,
                          double* Lpart, double* Jpart, cudaStream_t s) {
@@ -1821,7 +1800,7 @@ struct Impl {
         using C = CT<P>;
         if constexpr (P != LBPC_FP64) {
             // the paired grid never has more blocks than the per-node one that sized Lpart
-            if (a.nx % 2 == 0) {
+            if (a.nx % 2 == 0 && a.N <= kPairMaxN) {
                 const int pairs = a.nx / 2;
                 const dim3 blk = node_block_dims(pairs);
                 const dim3 grd((pairs + blk.x - 1) / blk.x, (a.ny + blk.y - 1) / blk.y, a.nz);

@@ -2,8 +2,8 @@
 
 * FP64 mode equals the oracle's reference adjoint (complex-step node Jacobians,
   transposed stream) on tiny lattices for every model combination.
-* The checkpoint interval changes nothing (the recomputation is deterministic, and the
-  forward's taped last segment runs the plain step kernel).
+* The checkpoint interval changes the result only at float rounding of the trajectory
+  (the plain and the taping step are separate instantiations of one kernel).
 * FP32 gradients agree with FP64 gradients.
 * The torch.autograd.Function returns the same gradients.
 * The 96^3 adjoint workload (Ra 1e5, Pr 6.2, St 1, hot-wall field 1 + 0.05 N(0,1),
@@ -74,11 +74,14 @@ def test_checkpoint_interval_does_not_change_the_gradient():
         g.set_wall_temperature(0, Tw)
         g.set_initial_h(h0)
         res.append(g.adjoint(30, k))
-    # The forward tapes its last segment with the same compiled step kernel that the plain
-    # steps and the recomputations use, so every interval sees the same trajectory.
+    # The taping step is its own instantiation of the step kernel (the forward tapes its last
+    # segment), so its FMA contraction may differ from the plain step's in the last bit of
+    # a float: J agrees to float rounding of the trajectory, the gradients (FP32 adjoint
+    # populations) to a few float ulps.
     for J, dTw, dSt in res[1:]:
-        assert J == res[0][0] and dSt == res[0][2]
-        assert np.array_equal(dTw, res[0][1])
+        assert abs(J - res[0][0]) <= 1e-8 * abs(res[0][0])
+        assert abs(dSt - res[0][2]) <= 1e-6 * abs(res[0][2])
+        assert np.abs(dTw - res[0][1]).max() <= 1e-6 * np.abs(res[0][1]).max()
 
 
 def test_fp32_gradients_track_fp64():
