@@ -53,9 +53,10 @@ def _kernel_hash():
     return h.hexdigest()[:16]
 
 
-def _traffic_per_lup(precision):
-    """DRAM bytes per lattice update of the step kernel from the committed ncu summary,
-    valid only while the kernel sources hash to the recorded value."""
+def _traffic_per_lup(precision, streaming=inp.PULL):
+    """DRAM bytes per lattice update of the step kernel from the committed ncu summary
+    (one full-size launch, read + write), valid only while the kernel sources hash to the
+    recorded value."""
     path = os.path.join(ROOT, "profiles", "step_kernel_traffic.txt")
     if not os.path.exists(path):
         return None
@@ -67,7 +68,8 @@ def _traffic_per_lup(precision):
             rec[k.strip()] = v.strip()
     if rec.get("kernel_sources_sha256_16") != _kernel_hash():
         return None
-    key = f"dram_bytes_per_lup_{inp.PRECISION_NAMES[precision]}"
+    key = f"dram_bytes_per_lup_{inp.PRECISION_NAMES[precision]}" + (
+        "_aa" if streaming == inp.AA else "")
     return float(rec[key]) if key in rec else None
 
 
@@ -251,8 +253,10 @@ def run_ours(args):
     from paper_1703_02652_gb300 import LBPC
 
     w = inp.bench_workload()
-    if args.lattice != 256:  # smaller cavity of the same physics, for profiling
-        w = inp.cavity_melting(n=args.lattice, Ra=1e6, Pr=0.02, St=1.0, precision=inp.FP32,
+    if args.lattice != 256 or args.pr != 0.02:
+        # the same cavity at another size (profiling cases; the 512^3 throughput-ceiling
+        # lines) or Prandtl number (512^3 is quoted at Pr = 50)
+        w = inp.cavity_melting(n=args.lattice, Ra=1e6, Pr=args.pr, St=1.0, precision=inp.FP32,
                                steps=w.steps, report_every=w.params.report_every)
     precision = {"f32": inp.FP32, "f16": inp.FP16, "bf16": inp.BF16, "f64": inp.FP64,
                  "f16g32": inp.FP16_G32, "bf16g32": inp.BF16_G32}[args.precision]
@@ -315,7 +319,7 @@ def run_ours(args):
     peak, peak_kind = _peaks()
     bpl = BYTES_PER_LUP[precision]
     achieved = per_rank * 1e6 * bpl / 1e9
-    tr = _traffic_per_lup(precision)
+    tr = _traffic_per_lup(precision, streaming)
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -363,7 +367,9 @@ def main():
     ap.add_argument("--precision", default="f32",
                     choices=["f32", "f16", "bf16", "f64", "f16g32", "bf16g32"])
     ap.add_argument("--streaming", default="pull", choices=["pull", "aa"])
-    ap.add_argument("--lattice", type=int, default=256, help="cavity edge (profiling only)")
+    ap.add_argument("--lattice", type=int, default=256,
+                    help="cavity edge (256: the benchmark; 128: profiling; 512: ceiling lines)")
+    ap.add_argument("--pr", type=float, default=0.02, help="Prandtl number of the cavity")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
