@@ -32,7 +32,7 @@
 extern "C" {
 #endif
 
-#define LBPC_ABI_VERSION 1
+#define LBPC_ABI_VERSION 2
 
 typedef enum lbpc_status {
     LBPC_OK = 0,
@@ -78,6 +78,12 @@ enum { LBPC_PULL = 0, LBPC_AA = 1 };
  *  h0          uniform initial enthalpy (lbpc_set_initial_h overrides per node).
  *  report_every > 0  record diagnostics every so many steps (lbpc_get_history) and check
  *              for divergence at the end of lbpc_step; 0 disables both.
+ *  lambda_s, lambda_l  both > 0: per-phase thermal conductivities (Eq. 1, rho0 = 1; Sec.
+ *              3.1.2 case (b)), conduction only (flow_model NONE, no tau_g).  The
+ *              enthalpy rates then follow per node from f_l: chi = lambda(f_l) / C_p,ref
+ *              with lambda(f_l) = lambda_s + f_l (lambda_l - lambda_s) (the paper gives no
+ *              mushy-zone rule), sigma_chi from Eq. 34, sigma_4..6 as set above.  The
+ *              adjoint refuses this mode (LBPC_ERR_STATE).  Both 0: one conductivity.
  */
 typedef struct lbpc_params {
     int flow_model;
@@ -95,6 +101,7 @@ typedef struct lbpc_params {
     double sigma4;
     double h0;
     int report_every;
+    double lambda_s, lambda_l;
 } lbpc_params;
 
 typedef struct lbpc_handle lbpc_handle;

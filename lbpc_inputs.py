@@ -60,6 +60,8 @@ class Params:
     sigma4: float = 0.0
     h0: float = 0.0
     report_every: int = 0
+    lambda_s: float = 0.0  # both > 0: per-phase conductivities (conduction only)
+    lambda_l: float = 0.0
 
     def replace(self, **kw) -> "Params":
         return dataclasses.replace(self, bc=list(self.bc), T_wall=list(self.T_wall), **kw)
@@ -105,6 +107,22 @@ def stefan_solidification(nx=64, ny=2, nz=2, chi=0.4, Ste=0.004, precision=FP64)
                T_wall=[-1.0, 0.0, 0.0, 0.0, 0.0, 0.0], St=Ste, Th=1.0, Tm=0.0,
                tau_g=tau_g, omega_T=omega_T, h0=L + 1.0)
     return Workload(f"stefan-solidification-{nx}", (nx, ny, nz), p, 4000)
+
+
+def stefan_solidification_b(nx=128, ny=2, nz=2, lambda_s=0.24, precision=FP64) -> Workload:
+    """Sec. 3.1.2 case (b): C_p,s = 1, C_p,l = 2, Ste_s = 0.004, Ste_l = 0.008 and
+    lambda_s / lambda_l = 0.6 / 0.15, so chi_s / chi_l = 8 (lattice units: lambda_s given,
+    rho0 = C_p,ref = 1).  Initially liquid at T_0 = 1, wall at T_1 = -1, T_m = 0:
+    L = C_p,l (T_0 - T_m) / Ste_l = 250, i.e. St = Ste_l with Th = T_0."""
+    lambda_l = lambda_s * 0.15 / 0.6
+    Cp_s, Cp_l = 1.0, 2.0
+    L = Cp_l * 1.0 / 0.008
+    p = Params(flow_model=FLOW_NONE, enth_model=ENTH_MRT, precision=precision,
+               bc=[ISOTHERMAL, ADIABATIC, PERIODIC, PERIODIC, PERIODIC, PERIODIC],
+               T_wall=[-1.0, 0.0, 0.0, 0.0, 0.0, 0.0], St=0.008, Th=1.0, Tm=0.0,
+               Cp_s=Cp_s, Cp_l=Cp_l, Cp_ref=1.0, omega_T=0.25,
+               lambda_s=lambda_s, lambda_l=lambda_l, h0=L + Cp_l * 1.0)
+    return Workload(f"stefan-solidification-b-{nx}", (nx, ny, nz), p, 20000)
 
 
 def cavity_melting(n=64, Ra=1e5, Pr=0.02, St=1.0, precision=FP32, streaming=PULL,

@@ -74,6 +74,7 @@ struct orc_state {
     /* derived lattice constants */
     double dT, L, hs, hl, chi, nu, gbeta, U0, H;
     double tau_g, tau_f, sigma[7], lam[19];
+    int varchi;             /* per-phase conductivities: rates per node from f_l */
     double Minv[19][19], Ninv[7][7];
     int opp19[19], opp7[7];
     /* state */
@@ -189,6 +190,18 @@ static int map_params(orc_state *s) {
         s->gbeta = s->U0 * s->U0 / (s->dT * s->H);
     }
     if (p->tau_g > 0) s->chi = (p->tau_g - 0.5) * p->omega_T; /* Eq. 20 */
+    s->varchi = p->lambda_s > 0 || p->lambda_l > 0;
+    if (s->varchi) {
+        /* Per-phase conductivities (Sec. 3.1.2 case (b)).  Eq. 1 diffuses with lambda/rho0
+         * and Eq. 33 with chi acting on C_p,ref T, so chi = lambda / (rho0 C_p,ref), rho0 = 1;
+         * the relaxation rates then follow per node from f_l (orc_collide_node).  The
+         * constants below use the solid value. */
+        if (p->lambda_s <= 0 || p->lambda_l <= 0) { set_err("give both lambda_s and lambda_l"); return -1; }
+        if (p->flow_model != ORC_FLOW_NONE || p->tau_g > 0) {
+            set_err("per-phase conductivities need flow_model NONE and no tau_g"); return -1;
+        }
+        s->chi = p->lambda_s / p->Cp_ref;
+    }
     if (s->chi <= 0) { set_err("thermal diffusivity undefined: give tau_g or the flow groups"); return -1; }
     /* Eq. 20 / Eq. 34: chi = (tau_g - 1/2) omega_T = (1/sigma_chi - 1/2) omega_T */
     s->tau_g = s->chi / p->omega_T + 0.5;
@@ -377,11 +390,24 @@ void orc_collide_node(const orc_state *s, const double *f, const double *g, doub
         }
     }
     /* 5b. enthalpy collision */
+    const double *sigma = s->sigma;
+    double tau_g = s->tau_g, sigma_n[7];
+    if (s->varchi) {
+        /* READING: the paper gives no mushy-zone rule for lambda; lambda(f_l) = lambda_s +
+         * f_l (lambda_l - lambda_s), then chi = lambda / C_p,ref and Eq. 34 per node */
+        const double chi_n = (p->lambda_s + fl * (p->lambda_l - p->lambda_s)) / p->Cp_ref;
+        const double sc = 1.0 / (chi_n / p->omega_T + 0.5);
+        for (int k = 0; k < 7; k++) sigma_n[k] = sc;
+        sigma_n[0] = 1.0;
+        sigma_n[4] = sigma_n[5] = sigma_n[6] = p->sigma4 > 0 ? p->sigma4 : 2.0 - sc; /* Eq. 47 */
+        sigma = sigma_n;
+        tau_g = 1.0 / sc;
+    }
     if (p->enth_model == ORC_ENTH_SRT) {
         /* Eq. 5-7: BGK relaxation towards g^eq */
         double geq[7];
         orc_enth_geq(s, h, T, fl, u, geq);
-        for (int a = 0; a < 7; a++) gpost[a] = g[a] - (g[a] - geq[a]) / s->tau_g;
+        for (int a = 0; a < 7; a++) gpost[a] = g[a] - (g[a] - geq[a]) / tau_g;
     } else {
         /* Eq. 21-25: relaxation of the moments n = N g */
         double n[7], neq[7], np[7];
@@ -390,7 +416,7 @@ void orc_collide_node(const orc_state *s, const double *f, const double *g, doub
             for (int a = 0; a < 7; a++) n[k] += NMAT[k][a] * g[a];
         }
         orc_enth_neq(s, h, T, fl, u, neq);
-        for (int k = 0; k < 7; k++) np[k] = n[k] - s->sigma[k] * (n[k] - neq[k]);
+        for (int k = 0; k < 7; k++) np[k] = n[k] - sigma[k] * (n[k] - neq[k]);
         for (int a = 0; a < 7; a++) {
             gpost[a] = 0.0;
             for (int k = 0; k < 7; k++) gpost[a] += s->Ninv[a][k] * np[k];

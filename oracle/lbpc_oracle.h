@@ -37,6 +37,7 @@ typedef struct orc_params {
     double s_e, s_eps, s_q, s_pi, s_t; /* flow non-hydrodynamic rates (<= 0: default) */
     double sigma4;         /* <= 0: sigma4 = sigma5 = sigma6 = 2 - sigma_chi (Eq. 47) */
     double h0;             /* uniform initial enthalpy */
+    double lambda_s, lambda_l; /* both > 0: per-phase conductivities (Eq. 1), conduction only */
 } orc_params;
 
 typedef struct orc_state orc_state;

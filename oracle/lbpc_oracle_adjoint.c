@@ -211,6 +211,8 @@ int orc_adjoint(orc_state *s, int nsteps, int wface, double *J_out, double *dJ_d
     orc__dims(s, &nx, &ny, &nz);
     const long NN = (long)nx * ny * nz;
     const orc_params *p = orc__params(s);
+    /* the node Jacobians below use the constant relaxation rates */
+    if (p->lambda_s > 0 || p->lambda_l > 0) return -1;
     const int flow = p->flow_model != ORC_FLOW_NONE;
     const int nf = flow ? 19 : 0, nv = nf + 7;
     double Lr, hs, gbeta, sigma[7], lam[19];

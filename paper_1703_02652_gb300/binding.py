@@ -39,7 +39,8 @@ class LbpcParams(C.Structure):
                 ("streaming", C.c_int), ("bc", C.c_int * 6), ("T_wall", C.c_double * 6)] + [
         (n, C.c_double) for n in ("Ra", "Pr", "St", "Ma", "Th", "Tm", "Tref", "Cp_s", "Cp_l",
                                   "Cp_ref", "omega_T", "tau_g", "nu", "s_e", "s_eps", "s_q",
-                                  "s_pi", "s_t", "sigma4", "h0")] + [("report_every", C.c_int)]
+                                  "s_pi", "s_t", "sigma4", "h0")] + [("report_every", C.c_int)] + [
+        ("lambda_s", C.c_double), ("lambda_l", C.c_double)]
 
 
 class LbpcError(RuntimeError):

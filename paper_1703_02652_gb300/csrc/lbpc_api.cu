@@ -687,6 +687,8 @@ lbpc_status lbpc_adjoint_forward(lbpc_handle* h, int nsteps, int ckpt_every, voi
     if (!h) return LBPC_ERR_PARAM;
     if (nsteps < 1 || ckpt_every < 1) return fail(h, LBPC_ERR_PARAM, "nsteps and ckpt_every must be >= 1");
     if (h->p.streaming != LBPC_PULL) return fail(h, LBPC_ERR_STATE, "the adjoint needs pull streaming");
+    if (h->p.lambda_s > 0 || h->p.lambda_l > 0)
+        return fail(h, LBPC_ERR_STATE, "the adjoint needs one conductivity (no lambda_s / lambda_l)");
     if (h->diverged) return fail(h, LBPC_ERR_STATE, "state diverged");
     const AdjLayout L = adj_layout(h, nsteps, ckpt_every);
     if (!dev_ws || ((uintptr_t)dev_ws) % kAlign != 0 || ws_bytes < L.total)

@@ -55,6 +55,16 @@ inline bool validate_and_map(int nx, int ny, int nz, const lbpc_params* p, Deriv
         if (!(p->tau_g > 0.5)) { e = "tau_g must exceed 1/2"; return false; }
         d.chi = (p->tau_g - 0.5) * p->omega_T;  // Eq. 20
     }
+    const bool varchi = p->lambda_s > 0 || p->lambda_l > 0;
+    if (varchi) {
+        // per-phase conductivities (Sec. 3.1.2 case (b)): chi = lambda / (rho0 C_p,ref) per
+        // node; the constants use the solid value
+        if (!(p->lambda_s > 0 && p->lambda_l > 0)) { e = "give both lambda_s and lambda_l"; return false; }
+        if (p->flow_model != LBPC_FLOW_NONE || p->tau_g > 0) {
+            e = "per-phase conductivities need flow_model NONE and no tau_g"; return false;
+        }
+        d.chi = p->lambda_s / p->Cp_ref;
+    }
     if (!(d.chi > 0)) { e = "no thermal diffusivity: give tau_g > 1/2 or a flow model"; return false; }
     d.tau_g = d.chi / p->omega_T + 0.5;  // Eq. 20 / Eq. 34 solved for the relaxation time
     d.sigma_chi = 1.0 / d.tau_g;
@@ -136,6 +146,15 @@ inline void fill_coef(Coef<C>& c, const lbpc_params& p, const Derived& d) {
     c.sig6_4 = (C)(d.sigma4 / 4.0);
     c.hchi = (C)(0.5 * d.sigma_chi);
     c.dCp = (C)(p.Cp_l - p.Cp_s);
+    // per-phase conductivities: 1/sigma_chi = chi_a + chi_b f_l (Eq. 34 with chi =
+    // lambda(f_l) / C_p,ref); sigma_4 = s4_a + s4_b sigma_chi (2 - sigma_chi under Eq. 47,
+    // sigma_chi for SRT, or the fixed value)
+    c.varchi = p.lambda_s > 0 || p.lambda_l > 0;
+    c.chi_a = (C)(0.5 + p.lambda_s / (p.omega_T * p.Cp_ref));
+    c.chi_b = (C)((p.lambda_l - p.lambda_s) / (p.omega_T * p.Cp_ref));
+    const bool srt = p.enth_model == LBPC_ENTH_SRT;
+    c.s4_a = (C)(srt ? 0.0 : (p.sigma4 > 0 ? p.sigma4 : 2.0));
+    c.s4_b = (C)(srt ? 1.0 : (p.sigma4 > 0 ? 0.0 : -1.0));
     c.gshift2 = (C)(gshifted ? p.omega_T * p.Cp_ref * p.Tref : 0.0);
 }
 

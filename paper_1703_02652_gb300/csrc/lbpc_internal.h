@@ -26,6 +26,9 @@ struct Coef {
         c_pi12, r_nu13, c_nu13, r_t;
     // D3Q7 relaxation: sig4 / 6, sig5 / 6, sig6 / 4, sig_chi / 2; Cp_l - Cp_s; 2 gshift
     C sig4_6, sig5_6, sig6_4, hchi, dCp, gshift2;
+    // per-phase conductivities (conduction only): rates per node from f_l
+    int varchi;
+    C chi_a, chi_b, s4_a, s4_b;
 };
 
 struct Args {

@@ -541,7 +541,8 @@ LBPC_HD void collide_flow(C* f, const Coef<C>& k, C T, C fl, C& ux, C& uy, C& uz
 // D3Q7 enthalpy collision on the six moving populations (Eq. 21-25; SRT when every
 // rate equals 1/tau_g).  With d_a = g_a - g_a^eq, d_0 = -sum d_a (h is conserved), the
 // moments of d are m1..m3 (odd pairs), m4 = -7 S, m5, m6; g* = g^eq + d - N^-1 R N d.
-template <class C>
+// VAR (conduction kernels): with per-phase conductivities the rates follow from f_l.
+template <class C, bool VAR = false>
 LBPC_HD void collide_enth(C* g, const Coef<C>& k, C T, C fl, C ux, C uy, C uz) {
     const C Cp = k.Cps + fl * k.dCp;
     // an axis pair's equilibria (Eq. 7) sum to cT2 (representation) and differ by vT2 u
@@ -555,10 +556,19 @@ LBPC_HD void collide_enth(C* g, const Coef<C>& k, C T, C fl, C ux, C uy, C uz) {
     const C q = p34 + p56;
     const C S = p12 + q, m5 = C(2) * p12 - q, m6 = p34 - p56;
     // g* = g^eq + d - N^-1 R N d = g - N^-1 R N d, rates and 1/|row|^2 folded on the host
-    const C A = k.sig4_6 * S, B = k.sig5_6 * m5, D = k.sig6_4 * m6;
+    C s46 = k.sig4_6, s56 = k.sig5_6, s64 = k.sig6_4, hchi = k.hchi;
+    if (VAR && k.varchi) {  // Eq. 34 per node, lambda(f_l) linear in f_l
+        const C sc = C(1) / (k.chi_a + k.chi_b * fl);
+        const C s4 = k.s4_a + k.s4_b * sc;
+        s46 = s4 * C(1.0 / 6.0);
+        s56 = s46;
+        s64 = s4 * C(0.25);
+        hchi = C(0.5) * sc;
+    }
+    const C A = s46 * S, B = s56 * m5, D = s64 * m6;
     const C c12 = A + B, c36 = A - C(0.5) * B;
     const C c3p = c36 + D, c3m = c36 - D;
-    const C h1 = k.hchi * m1, h2 = k.hchi * m2, h3 = k.hchi * m3;
+    const C h1 = hchi * m1, h2 = hchi * m2, h3 = hchi * m3;
     g[1] -= c12 + h1;
     g[2] -= c12 - h1;
     g[3] -= c3p + h2;
@@ -665,7 +675,7 @@ LBPC_HD void step_node(const Args& a, int x, int y, int z, const TF<P>* fs,
             tape_m[3 * (size_t)a.N + n] = jz;
         }
     }
-    collide_enth(g, k, T, fl, ux, uy, uz);
+    collide_enth<C, !FLOW>(g, k, T, fl, ux, uy, uz);
     if (interior) {
         if constexpr (FLOW) scatter_f<Mode<P>::F, KIND>(a, bi, n, fd, f);
         scatter_g<Mode<P>::G, KIND>(a, bi, n, x, y, z, gd, g);
@@ -704,8 +714,8 @@ LBPC_HD void pair_collide(const Args& a, CT<P>* f0, CT<P>* f1, CT<P>* g0, CT<P>*
     }
     if constexpr (TAPE)
         *reinterpret_cast<VC*>(tape_e + n0) = VC{to_compute(e0, C(0)), to_compute(e1, C(0))};
-    collide_enth(g0, k, T0, fl0, ux0, uy0, uz0);
-    collide_enth(g1, k, T1, fl1, ux1, uy1, uz1);
+    collide_enth<C, !FLOW>(g0, k, T0, fl0, ux0, uy0, uz0);
+    collide_enth<C, !FLOW>(g1, k, T1, fl1, ux1, uy1, uz1);
 }
 
 // Two nodes (x0, x0 + 1), x0 even, of a row away from every y and z face: populations

@@ -161,6 +161,12 @@ def test_adjoint_error_paths():
     with pytest.raises(LbpcError) as e:
         g.adjoint_backward(0)
     assert e.value.status == B.LBPC_ERR_STATE
+    w = inp.stefan_solidification_b(nx=8, ny=3, nz=3)  # per-phase conductivities
+    g = LBPC(w.shape, w.params)
+    g.set_initial_h(inp.h0_field(w))
+    with pytest.raises(LbpcError) as e:
+        g.adjoint(5, 2)
+    assert e.value.status == B.LBPC_ERR_STATE
 
 
 def test_adjoint_workload_96_finite_differences():

@@ -2,7 +2,7 @@
 
 * Eq. 61: the melting root reproduces the interface position the paper prints.
 * Eq. 60-61: 1D melting of a half-space (the 64x4x4 conduction workload).
-* Eq. 62-63: 1D solidification, Sec. 3.1.2 case (a).
+* Eq. 62-63: 1D solidification, Sec. 3.1.2 cases (a) and (b) (per-phase C_p and lambda).
 * Eq. 20 / Eq. 34: the decay rate of a sinusoidal conduction mode gives back the
   diffusivity fixed by the relaxation time.
 * Eq. 47 (Sec. 2.4): with sigma_1 + sigma_4 = 2 the solid ahead of the front stays
@@ -76,6 +76,61 @@ def test_stefan_solidification_case_a():
     x = np.arange(w.shape[0]) + 0.5
     Ta = nm.solidification_temperature(x, t, 0.4, 0.4, k)
     assert np.abs(F["T"][0, 0, :] - Ta).max() < 0.01
+
+
+def test_solidification_root_case_b():
+    # Sec. 3.1.2 case (b): Ste_s = 0.004, Ste_l = 0.008, chi_s / chi_l = (0.6/1) / (0.15/2) = 8
+    k = nm.solidification_k(0.004, 0.008, 0.6, 0.075)
+    r = math.sqrt(8.0)
+    lhs = 0.004 / (math.exp(k * k) * math.erf(k)) - 0.008 / r / (
+        math.exp(k * k * 8.0) * math.erfc(k * r))
+    assert abs(lhs - k * math.sqrt(math.pi)) < 1e-12
+    assert abs(k - 0.0437895) < 5e-7
+    # only the ratio of the diffusivities enters k
+    assert abs(nm.solidification_k(0.004, 0.008, 1.0, 0.125) - k) < 1e-12
+
+
+def test_per_phase_conductivity_reduces_to_one_conductivity():
+    """lambda_s = lambda_l = lambda gives the constant-rate model with tau_g =
+    lambda / (omega_T C_p,ref) + 1/2 (Eq. 34 with chi = lambda / C_p,ref)."""
+    w = inp.stefan_solidification_b(nx=24, ny=2, nz=2, lambda_s=0.3)
+    h0 = inp.h0_field(w)
+    a = w.params.replace(lambda_l=0.3)
+    b = w.params.replace(lambda_s=0.0, lambda_l=0.0, tau_g=0.3 / 0.25 + 0.5)
+    res = []
+    for p in (a, b):
+        o = oracle.Oracle(w.shape, p)
+        o.set_initial_h(h0)
+        o.step(400)
+        res.append(o.fields())
+    assert np.abs(res[0]["T"] - res[1]["T"]).max() < 1e-13
+    assert np.abs(res[0]["h"] - res[1]["h"]).max() < 1e-10
+
+
+def test_stefan_solidification_case_b():
+    """Sec. 3.1.2 case (b): C_p,l = 2 C_p,s, lambda_s = 4 lambda_l (chi_s = 8 chi_l), Ste_s =
+    0.004, Ste_l = 0.008, per-node rates from f_l.  Lattice: lambda_s = 1 (chi_s = 1,
+    chi_l = 1/8), 256 nodes.  The front trails the Neumann solution (Eq. 63) by a fixed
+    fraction of a cell -- the rate jumps from node to node at the front -- so its relative
+    error shrinks as the front advances; the liquid temperature follows Eq. 62."""
+    w = inp.stefan_solidification_b(nx=256, lambda_s=1.0)
+    o = oracle.Oracle(w.shape, w.params)
+    o.set_initial_h(inp.h0_field(w))
+    chi_s, chi_l = 1.0, 0.125
+    k = nm.solidification_k(0.004, 0.008, chi_s, chi_l)
+    x = np.arange(w.shape[0]) + 0.5
+    errs = []
+    for t in (10000, 20000):
+        o.step(t - int(o.diagnostics()["step"]))
+        F = o.fields()
+        X = float(nm.solidification_front(t, chi_s, k))
+        depth = (1.0 - F["fl"][0, 0, :]).sum()
+        errs.append((depth - X) / X)
+        assert X - depth < 0.7  # lag below one cell
+        Ta = nm.solidification_temperature(x, t, chi_s, chi_l, k)
+        liquid = (x > X + 3) & (x < X + 4 * math.sqrt(chi_l * t))
+        assert np.abs(F["T"][0, 0, liquid] - Ta[liquid]).max() < 0.01
+    assert abs(errs[1]) < 0.04 and abs(errs[1]) < abs(errs[0])
 
 
 def _decay_rate(nx, params, t1=300, t2=900):
