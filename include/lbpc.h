@@ -32,7 +32,7 @@
 extern "C" {
 #endif
 
-#define LBPC_ABI_VERSION 2
+#define LBPC_ABI_VERSION 3
 
 typedef enum lbpc_status {
     LBPC_OK = 0,
@@ -84,6 +84,11 @@ enum { LBPC_PULL = 0, LBPC_AA = 1 };
  *              with lambda(f_l) = lambda_s + f_l (lambda_l - lambda_s) (the paper gives no
  *              mushy-zone rule), sigma_chi from Eq. 34, sigma_4..6 as set above.  The
  *              adjoint refuses this mode (LBPC_ERR_STATE).  Both 0: one conductivity.
+ *  darcy_A > 0 replaces the liquid-fraction solid closure (u = f_l u*, F_s = -2 (1 - f_l)
+ *              rho0 u*) by an enthalpy-porosity drag F_s = -D rho0 u with D = darcy_A
+ *              (1 - f_l)^2 / (f_l^3 + darcy_eps) (darcy_eps <= 0: 1e-3), solved together
+ *              with u = u* + F_s / 2: u = phi u*, phi = 1 / (1 + D/2).  Not in the paper (a
+ *              common alternative closure); the adjoint differentiates it.  0: the paper's.
  */
 typedef struct lbpc_params {
     int flow_model;
@@ -102,6 +107,7 @@ typedef struct lbpc_params {
     double h0;
     int report_every;
     double lambda_s, lambda_l;
+    double darcy_A, darcy_eps;
 } lbpc_params;
 
 typedef struct lbpc_handle lbpc_handle;

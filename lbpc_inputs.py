@@ -62,6 +62,8 @@ class Params:
     report_every: int = 0
     lambda_s: float = 0.0  # both > 0: per-phase conductivities (conduction only)
     lambda_l: float = 0.0
+    darcy_A: float = 0.0  # > 0: enthalpy-porosity solid drag instead of the f_l closure
+    darcy_eps: float = 0.0  # <= 0: 1e-3
 
     def replace(self, **kw) -> "Params":
         return dataclasses.replace(self, bc=list(self.bc), T_wall=list(self.T_wall), **kw)
@@ -136,6 +138,20 @@ def cavity_melting(n=64, Ra=1e5, Pr=0.02, St=1.0, precision=FP32, streaming=PULL
     shape = tuple(shape) if shape is not None else (n, n, n)
     name = f"cavity-melting-{shape[0]}x{shape[1]}x{shape[2]}-Ra{Ra:g}-Pr{Pr:g}-St{St:g}"
     return Workload(name, shape, p, steps, seed=0, perturb=1e-6)
+
+
+def cavity_melting_2d(n=64, Ra=2.5e4, Pr=0.02, St=0.01, precision=FP32, steps=100000,
+                      report_every=0) -> Workload:
+    """Quasi-2D convective melting (Sec. 3.2.2, Table 1): a 1 x 1 cavity in x-z, infinite
+    along y (one periodic node); hot wall x = -1/2 at T = 1, cold wall x = n - 1/2 at
+    T = T_m = 0, top and bottom (z) adiabatic, all walls no-slip; gravity along -z;
+    initially solid at T_m with a seeded +-1e-6 enthalpy perturbation."""
+    p = Params(flow_model=FLOW_MRT, enth_model=ENTH_MRT, precision=precision,
+               bc=[ISOTHERMAL, ISOTHERMAL, PERIODIC, PERIODIC, ADIABATIC, ADIABATIC],
+               T_wall=[1.0, 0.0, 0.0, 0.0, 0.0, 0.0], Ra=Ra, Pr=Pr, St=St,
+               report_every=report_every)
+    return Workload(f"cavity-melting-2d-{n}x1x{n}-Ra{Ra:g}-Pr{Pr:g}-St{St:g}", (n, 1, n), p,
+                    steps, seed=0, perturb=1e-6)
 
 
 def h0_field(w: Workload) -> np.ndarray:

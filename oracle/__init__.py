@@ -52,7 +52,8 @@ class _Params(C.Structure):
                 ("T_wall", C.c_double * 6)] + [
         (n, C.c_double) for n in ("Ra", "Pr", "St", "Ma", "Th", "Tm", "Tref", "Cp_s", "Cp_l",
                                   "Cp_ref", "omega_T", "tau_g", "nu", "s_e", "s_eps", "s_q",
-                                  "s_pi", "s_t", "sigma4", "h0", "lambda_s", "lambda_l")]
+                                  "s_pi", "s_t", "sigma4", "h0", "lambda_s", "lambda_l",
+                                  "darcy_A", "darcy_eps")]
 
 
 _lib = None

@@ -341,6 +341,13 @@ void orc_enth_neq(const orc_state *s, double h, double T, double fl, const doubl
     neq[6] = 0.0;
 }
 
+double orc_solid_phi(const orc_params *p, double fl) {
+    if (p->darcy_A <= 0) return fl;
+    const double eps = p->darcy_eps > 0 ? p->darcy_eps : 1e-3;
+    const double D = p->darcy_A * (1.0 - fl) * (1.0 - fl) / (fl * fl * fl + eps);
+    return 1.0 / (1.0 + 0.5 * D);
+}
+
 /* ---- one node: macroscopic quantities and both collisions ----
  * macro (optional, 10 values): h, T, f_l, rho, u[3], F[3]. */
 void orc_collide_node(const orc_state *s, const double *f, const double *g, double *fpost,
@@ -365,11 +372,13 @@ void orc_collide_node(const orc_state *s, const double *f, const double *g, doub
         double Fb[3] = {0.0, 0.0, s->gbeta * (T - p->Tref)};
         /* READING: solid-phase force. The flow lives in the liquid and the interface is
          * no-slip; the force -2 (1 - f_l) rho0 u* removes the fraction (1 - f_l) of
-         * the velocity u* = (j + F_b/2)/rho0, so u = f_l u* and u = 0 in the solid. */
+         * the velocity u* = (j + F_b/2)/rho0, so u = f_l u* and u = 0 in the solid.
+         * The enthalpy-porosity alternative (not in the paper) replaces f_l by phi. */
+        const double phi = orc_solid_phi(p, fl);
         double us[3], Fs[3];
         for (int d = 0; d < 3; d++) {
             us[d] = (j[d] + 0.5 * Fb[d]) / rho0;
-            Fs[d] = -2.0 * (1.0 - fl) * rho0 * us[d];
+            Fs[d] = -2.0 * (1.0 - phi) * rho0 * us[d];
             F[d] = Fb[d] + Fs[d];
             u[d] = (j[d] + 0.5 * F[d]) / rho0; /* Eq. 56 */
         }

@@ -38,7 +38,15 @@ typedef struct orc_params {
     double sigma4;         /* <= 0: sigma4 = sigma5 = sigma6 = 2 - sigma_chi (Eq. 47) */
     double h0;             /* uniform initial enthalpy */
     double lambda_s, lambda_l; /* both > 0: per-phase conductivities (Eq. 1), conduction only */
+    double darcy_A, darcy_eps; /* darcy_A > 0: enthalpy-porosity solid drag instead of the
+                                  liquid-fraction closure (darcy_eps <= 0: 1e-3) */
 } orc_params;
+
+/* Velocity factor of the solid-phase closure: u = phi u*, F_s = -2 (1 - phi) rho0 u*.
+ * phi = f_l (the liquid-fraction closure), or, with darcy_A > 0, the drag F_s = -D rho0 u
+ * with D = A (1 - f_l)^2 / (f_l^3 + eps) solved together with u = u* + F_s / (2 rho0):
+ * phi = 1 / (1 + D / 2). */
+double orc_solid_phi(const orc_params *p, double fl);
 
 typedef struct orc_state orc_state;
 

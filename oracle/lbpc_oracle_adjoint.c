@@ -93,9 +93,15 @@ static void collide_cs(const orc_state *s, const cplx *f, const cplx *g, cplx L,
             for (int d = 0; d < 3; d++) j[d] += f[a] * E19c[a][d];
         }
         cplx Fb[3] = {0, 0, gbeta * (T - p->Tref)}, F[3];
+        cplx phi = fl;  /* orc_solid_phi, in complex arithmetic */
+        if (p->darcy_A > 0) {
+            const double eps = p->darcy_eps > 0 ? p->darcy_eps : 1e-3;
+            const cplx D = p->darcy_A * (1.0 - fl) * (1.0 - fl) / (fl * fl * fl + eps);
+            phi = 1.0 / (1.0 + 0.5 * D);
+        }
         for (int d = 0; d < 3; d++) {
             cplx us = j[d] + 0.5 * Fb[d];
-            F[d] = Fb[d] - 2.0 * (1.0 - fl) * us;
+            F[d] = Fb[d] - 2.0 * (1.0 - phi) * us;
             u[d] = j[d] + 0.5 * F[d];
         }
         cplx ux = u[0], uy = u[1], uz = u[2], u2 = ux * ux + uy * uy + uz * uz;

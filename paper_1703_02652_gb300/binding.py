@@ -40,7 +40,8 @@ class LbpcParams(C.Structure):
         (n, C.c_double) for n in ("Ra", "Pr", "St", "Ma", "Th", "Tm", "Tref", "Cp_s", "Cp_l",
                                   "Cp_ref", "omega_T", "tau_g", "nu", "s_e", "s_eps", "s_q",
                                   "s_pi", "s_t", "sigma4", "h0")] + [("report_every", C.c_int)] + [
-        ("lambda_s", C.c_double), ("lambda_l", C.c_double)]
+        ("lambda_s", C.c_double), ("lambda_l", C.c_double), ("darcy_A", C.c_double),
+        ("darcy_eps", C.c_double)]
 
 
 class LbpcError(RuntimeError):

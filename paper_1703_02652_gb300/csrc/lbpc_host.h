@@ -34,6 +34,9 @@ inline bool validate_and_map(int nx, int ny, int nz, const lbpc_params* p, Deriv
     if (!(p->omega_T > 0.0 && p->omega_T <= 1.0 / 3.0)) { e = "omega_T must lie in (0, 1/3]"; return false; }
     if (!(p->Cp_s > 0 && p->Cp_l > 0 && p->Cp_ref > 0)) { e = "specific heats must be > 0"; return false; }
     if (!(p->St > 0)) { e = "St must be > 0"; return false; }
+    if (!(p->darcy_A >= 0) || !(p->darcy_A < 1e300) || !(p->darcy_eps < 1e300)) {
+        e = "darcy_A must be >= 0 and finite"; return false;
+    }
     d.dT = p->Th - p->Tm;
     if (!(d.dT > 0)) { e = "Th must exceed Tm"; return false; }
     // Stefan number (Eq. 64) fixes the latent heat; Eq. 2 with h0 = 0 gives h_s and h_l.
@@ -155,6 +158,9 @@ inline void fill_coef(Coef<C>& c, const lbpc_params& p, const Derived& d) {
     const bool srt = p.enth_model == LBPC_ENTH_SRT;
     c.s4_a = (C)(srt ? 0.0 : (p.sigma4 > 0 ? p.sigma4 : 2.0));
     c.s4_b = (C)(srt ? 1.0 : (p.sigma4 > 0 ? 0.0 : -1.0));
+    c.darcy = p.darcy_A > 0;
+    c.darcy_A = (C)p.darcy_A;
+    c.darcy_eps = (C)(p.darcy_eps > 0 ? p.darcy_eps : 1e-3);
     c.gshift2 = (C)(gshifted ? p.omega_T * p.Cp_ref * p.Tref : 0.0);
 }
 

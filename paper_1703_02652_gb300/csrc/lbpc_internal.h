@@ -29,6 +29,9 @@ struct Coef {
     // per-phase conductivities (conduction only): rates per node from f_l
     int varchi;
     C chi_a, chi_b, s4_a, s4_b;
+    // enthalpy-porosity solid drag D = darcy_A (1 - f_l)^2 / (f_l^3 + darcy_eps)
+    int darcy;
+    C darcy_A, darcy_eps;
 };
 
 struct Args {

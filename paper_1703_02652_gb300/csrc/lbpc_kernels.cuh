@@ -396,8 +396,30 @@ LBPC_HD void invert_excess(const Coef<C>& k, double e, C& T, C& fl) {
     }
 }
 
-// Density, momentum, Boussinesq force (Eq. 55), solid-phase force -2 (1 - f_l) u* and the
-// velocity of Eq. 56 (rho_0 = 1): u = f_l (j + F_b / 2).
+// Velocity factor phi of the solid closure, u = phi u*, F_s = -2 (1 - phi) rho0 u*: the
+// liquid fraction itself, or with the enthalpy-porosity drag D = A (1 - f_l)^2 / (f_l^3 +
+// eps), F_s = -D rho0 u and u = u* + F_s / (2 rho0) give phi = 1 / (1 + D / 2).  dphi (if
+// given) receives dphi / df_l.
+template <class C>
+LBPC_HD C darcy_phi(const Coef<C>& k, C fl, C* dphi = nullptr) {
+    const C s = C(1) - fl, q = fl * fl * fl + k.darcy_eps;
+    const C D = k.darcy_A * s * s / q;
+    const C phi = C(1) / (C(1) + C(0.5) * D);
+    if (dphi) {
+        const C dD = k.darcy_A * (C(-2) * s * q - C(3) * fl * fl * s * s) / (q * q);
+        *dphi = C(-0.5) * phi * phi * dD;
+    }
+    return phi;
+}
+template <class C>
+LBPC_HD C solid_phi(const Coef<C>& k, C fl, C* dphi = nullptr) {
+    if (k.darcy) return darcy_phi(k, fl, dphi);
+    if (dphi) *dphi = C(1);
+    return fl;
+}
+
+// Density, momentum, Boussinesq force (Eq. 55), solid-phase force -2 (1 - phi) u* and the
+// velocity of Eq. 56 (rho_0 = 1): u = phi (j + F_b / 2), phi = solid_phi(f_l).
 template <class C>
 LBPC_HD void flow_macro(const C* f, const Coef<C>& k, C T, C fl, C& rho, C& jx,
                                            C& jy, C& jz, C& ux, C& uy, C& uz, C& Fx, C& Fy,
@@ -410,13 +432,14 @@ LBPC_HD void flow_macro(const C* f, const Coef<C>& k, C T, C fl, C& rho, C& jx,
     jz = (f[5] - f[6]) + (f[11] + f[12] - f[13] - f[14]) + (f[15] + f[16] - f[17] - f[18]);
     const C Fb = k.gbeta * (T - k.Tref);
     const C usx = jx, usy = jy, usz = jz + C(0.5) * Fb;
-    const C damp = C(-2) * (C(1) - fl);
+    const C phi = solid_phi(k, fl);
+    const C damp = C(-2) * (C(1) - phi);
     Fx = damp * usx;
     Fy = damp * usy;
     Fz = Fb + damp * usz;
-    ux = fl * usx;
-    uy = fl * usy;
-    uz = fl * usz;
+    ux = phi * usx;
+    uy = phi * usy;
+    uz = phi * usz;
 }
 
 // D3Q19 MRT collision with forcing (Eq. 49-54) in correction form:
@@ -638,7 +661,7 @@ template <> struct KindLayout<STEP_AA_ODD> { static constexpr int value = LAYOUT
 
 // One time step of node (x, y, z): gather (stream in, with wall rules), Eq. 2 inversion,
 // flow collision, enthalpy collision, scatter, FP64 rest channel update.
-template <int P, int KIND, bool FLOW, bool TAPE = false>
+template <int P, int KIND, int FLOW, bool TAPE = false>
 LBPC_HD void step_node(const Args& a, int x, int y, int z, const TF<P>* fs,
                        TF<P>* fd, const TG<P>* gs,
                        TG<P>* gd, double* hp, CT<P>* tape_e = nullptr,
@@ -665,7 +688,8 @@ LBPC_HD void step_node(const Args& a, int x, int y, int z, const TF<P>* fs,
     C T, fl;
     invert_excess(k, e, T, fl);
     C ux = C(0), uy = C(0), uz = C(0), rho = C(0), jx = C(0), jy = C(0), jz = C(0);
-    if constexpr (FLOW) collide_flow(f, k, T, fl, ux, uy, uz, rho, jx, jy, jz);
+    if constexpr (FLOW)  // FLOW 2: the drag closure, phi(f_l) in place of f_l
+        collide_flow(f, k, T, FLOW == 2 ? darcy_phi(k, fl) : fl, ux, uy, uz, rho, jx, jy, jz);
     if constexpr (TAPE) {  // macroscopic tape of the pre-collision state (adjoint)
         tape_e[n] = to_compute(e, C(0));  // what the inversion uses
         if constexpr (FLOW) {
@@ -689,7 +713,7 @@ LBPC_HD void step_node(const Args& a, int x, int y, int z, const TF<P>* fs,
 
 // Inversion and both collisions of a node pair (n0, n0 + 1), in registers; with TAPE also
 // the macroscopic tape of the pair's pre-collision state (adjoint).
-template <int P, bool FLOW, bool TAPE = false>
+template <int P, int FLOW, bool TAPE = false>
 LBPC_HD void pair_collide(const Args& a, CT<P>* f0, CT<P>* f1, CT<P>* g0, CT<P>* g1, double e0,
                           double e1, int n0 = 0, CT<P>* tape_e = nullptr,
                           CT<P>* tape_m = nullptr) {
@@ -702,8 +726,10 @@ LBPC_HD void pair_collide(const Args& a, CT<P>* f0, CT<P>* f1, CT<P>* g0, CT<P>*
     C ux0 = C(0), uy0 = C(0), uz0 = C(0), ux1 = C(0), uy1 = C(0), uz1 = C(0);
     if constexpr (FLOW) {
         C r0, jx0, jy0, jz0, r1, jx1, jy1, jz1;
-        collide_flow(f0, k, T0, fl0, ux0, uy0, uz0, r0, jx0, jy0, jz0);
-        collide_flow(f1, k, T1, fl1, ux1, uy1, uz1, r1, jx1, jy1, jz1);
+        collide_flow(f0, k, T0, FLOW == 2 ? darcy_phi(k, fl0) : fl0, ux0, uy0, uz0, r0, jx0,
+                     jy0, jz0);
+        collide_flow(f1, k, T1, FLOW == 2 ? darcy_phi(k, fl1) : fl1, ux1, uy1, uz1, r1, jx1,
+                     jy1, jz1);
         if constexpr (TAPE) {
             const size_t N = (size_t)a.N;
             *reinterpret_cast<VC*>(tape_m + n0) = VC{r0, r1};
@@ -723,7 +749,7 @@ LBPC_HD void pair_collide(const Args& a, CT<P>* f0, CT<P>* f1, CT<P>* g0, CT<P>*
 // rules (periodic wrap; at a wall the reflected population of the node itself) applied
 // by selecting a 32-bit element offset from the population's plane on the lanes at x = 0
 // / x = nx - 1; every store is a pair.  Requires even nx.
-template <int P, bool FLOW, bool TAPE = false>
+template <int P, int FLOW, bool TAPE = false>
 LBPC_HD void step_pair_pull(const Args& a, int x0, int y, int z, const TF<P>* fs,
                             TF<P>* fd, const TG<P>* gs,
                             TG<P>* gd, double* hp, CT<P>* tape_e = nullptr,
@@ -831,7 +857,7 @@ LBPC_HD void opaque(T& v) {
 // Odd step (swapped layout): f_q(x) is slot qbar at x - e_q (slot q at x behind a wall) and
 // f*_q goes to slot q at x + e_q (slot qbar at x behind a wall), with the wall rules of the
 // per-node path.  Each thread reads and writes the same set of slots, so in place is safe.
-template <int P, bool FLOW, bool ODD>
+template <int P, int FLOW, bool ODD>
 LBPC_HD void step_pair_aa(const Args& a, int x0, int y, int z, TF<P>* F, TG<P>* G, double* hp) {
     using SF = Store<Mode<P>::F>;
     using SG = Store<Mode<P>::G>;
@@ -1178,13 +1204,14 @@ LBPC_HD C collide_adjoint(const Coef<C>& k, C d, C rho, C jx, C jy, C jz, C* lf,
     C T, fl, dTde, dfde, dTdL, dfdL;
     invert_excess_d(k, d, T, fl, dTde, dfde, dTdL, dfdL);
     C ux = C(0), uy = C(0), uz = C(0), usx = C(0), usy = C(0), usz = C(0), damp = C(0);
-    C Fx = C(0), Fy = C(0), Fz = C(0);
+    C Fx = C(0), Fy = C(0), Fz = C(0), phi = fl, dphi = C(1);
     if constexpr (FLOW) {
         const C Fb = k.gbeta * (T - k.Tref);
+        phi = solid_phi(k, fl, &dphi);
         usx = jx; usy = jy; usz = jz + C(0.5) * Fb;
-        damp = C(-2) * (C(1) - fl);
+        damp = C(-2) * (C(1) - phi);
         Fx = damp * usx; Fy = damp * usy; Fz = Fb + damp * usz;
-        ux = fl * usx; uy = fl * usy; uz = fl * usz;
+        ux = phi * usx; uy = phi * usy; uz = phi * usz;
     }
     // enthalpy: g*_a = geq_a + K (g - geq)_a (a >= 1), g*_0 = h - sum_a g*_a
     const C lg0 = lg[0];
@@ -1267,10 +1294,11 @@ LBPC_HD C collide_adjoint(const Coef<C>& k, C d, C rho, C jx, C jy, C jz, C* lf,
         const C lFy = cf * uy - c23 * r6 - C(2) * v9 * uy + C(2) * v11 * uy + r13 * ux + r14 * uz + mu5;
         const C lFz = cf * uz - c23 * r8 - C(2) * v9 * uz - C(2) * v11 * uz + r14 * uy + r15 * ux + mu7;
         // u = f_l us, F = F_b z + damp us, us = j + F_b/2 z, F_b = g beta (T - T_ref)
-        const C lusx = fl * lux + damp * lFx;
-        const C lusy = fl * luy + damp * lFy;
-        const C lusz = fl * luz + damp * lFz;
-        lfl += lux * usx + luy * usy + luz * usz + C(2) * (lFx * usx + lFy * usy + lFz * usz);
+        const C lusx = phi * lux + damp * lFx;
+        const C lusy = phi * luy + damp * lFy;
+        const C lusz = phi * luz + damp * lFz;
+        lfl += dphi * (lux * usx + luy * usy + luz * usz +
+                       C(2) * (lFx * usx + lFy * usy + lFz * usz));
         const C lFb = lFz + C(0.5) * lusz;
         lT += k.gbeta * lFb;
         // lambda_f = lambda*_f + M^T lambda_m, lambda_m = (lrho, -s mu, lj, ...)
@@ -1494,7 +1522,7 @@ LBPC_HD double adj_reverse_pair(const Args& a, int x0, int y, int z, const CT<P>
     if (x >= a.nx || y >= a.ny) return;
 
 // One node per thread; with TAPE (pull) also the adjoint tape.
-template <int P, int KIND, bool FLOW, bool TAPE>
+template <int P, int KIND, int FLOW, bool TAPE>
 __global__ void __launch_bounds__(STEP_THREADS)
 k_step(const __grid_constant__ Args a, const TF<P>* fs, TF<P>* fd,
        const TG<P>* gs, TG<P>* gd, double* __restrict__ hp, CT<P>* __restrict__ tape_e,
@@ -1507,7 +1535,7 @@ k_step(const __grid_constant__ Args a, const TF<P>* fs, TF<P>* fd,
 // Pull step, two nodes per thread along x (even nx).  Warps whose rows all lie away
 // from the y and z faces take the paired path; others run the per-node path twice.
 // With TAPE also the adjoint tape.  Five blocks per SM (96 registers); four when taping.
-template <int P, bool FLOW, bool TAPE>
+template <int P, int FLOW, bool TAPE>
 __global__ void __launch_bounds__(STEP_THREADS, TAPE ? 4 : 5)
 k_step_pull_x2(const __grid_constant__ Args a, const TF<P>* fs,
                TF<P>* fd, const TG<P>* gs, TG<P>* gd,
@@ -1530,7 +1558,7 @@ k_step_pull_x2(const __grid_constant__ Args a, const TF<P>* fs,
 
 
 // AA step, two nodes per thread along x (even nx); same vote as the pull pair kernel.
-template <int P, bool FLOW, bool ODD>
+template <int P, int FLOW, bool ODD>
 __global__ void __launch_bounds__(STEP_THREADS, 4)
 k_step_aa_x2(const __grid_constant__ Args a, TF<P>* F, TG<P>* G, double* __restrict__ hp) {
     const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
@@ -1709,7 +1737,7 @@ struct Impl {
     using TGp = TG<P>;
 
     // TAPE (pull only): also write the adjoint tape of this step to tape_e / tape_m
-    template <int KIND, bool FLOW, bool TAPE = false>
+    template <int KIND, int FLOW, bool TAPE = false>
     static void step_k(const Args& a, const void* fs, void* fd, const void* gs, void* gd,
                        double* hp, cudaStream_t s, void* tape_e = nullptr,
                        void* tape_m = nullptr) {
@@ -1736,13 +1764,19 @@ struct Impl {
     static void step(const Args& a, StepKind kind, const void* fs, void* fd, const void* gs,
                      void* gd, double* hp, cudaStream_t s) {
         if (a.flow) {
-            if (kind == STEP_PULL) step_k<STEP_PULL, true>(a, fs, fd, gs, gd, hp, s);
-            else if (kind == STEP_AA_EVEN) step_k<STEP_AA_EVEN, true>(a, fs, fd, gs, gd, hp, s);
-            else step_k<STEP_AA_ODD, true>(a, fs, fd, gs, gd, hp, s);
+            if (coef<CT<P>>(a).darcy) {
+                if (kind == STEP_PULL) step_k<STEP_PULL, 2>(a, fs, fd, gs, gd, hp, s);
+                else if (kind == STEP_AA_EVEN) step_k<STEP_AA_EVEN, 2>(a, fs, fd, gs, gd, hp, s);
+                else step_k<STEP_AA_ODD, 2>(a, fs, fd, gs, gd, hp, s);
+            } else {
+                if (kind == STEP_PULL) step_k<STEP_PULL, 1>(a, fs, fd, gs, gd, hp, s);
+                else if (kind == STEP_AA_EVEN) step_k<STEP_AA_EVEN, 1>(a, fs, fd, gs, gd, hp, s);
+                else step_k<STEP_AA_ODD, 1>(a, fs, fd, gs, gd, hp, s);
+            }
         } else {
-            if (kind == STEP_PULL) step_k<STEP_PULL, false>(a, fs, fd, gs, gd, hp, s);
-            else if (kind == STEP_AA_EVEN) step_k<STEP_AA_EVEN, false>(a, fs, fd, gs, gd, hp, s);
-            else step_k<STEP_AA_ODD, false>(a, fs, fd, gs, gd, hp, s);
+            if (kind == STEP_PULL) step_k<STEP_PULL, 0>(a, fs, fd, gs, gd, hp, s);
+            else if (kind == STEP_AA_EVEN) step_k<STEP_AA_EVEN, 0>(a, fs, fd, gs, gd, hp, s);
+            else step_k<STEP_AA_ODD, 0>(a, fs, fd, gs, gd, hp, s);
         }
     }
 
@@ -1794,8 +1828,12 @@ struct Impl {
 
     static void step_tape(const Args& a, const void* fs, void* fd, const void* gs, void* gd,
                           double* hp, void* tape_e, void* tape_m, cudaStream_t s) {
-        if (a.flow) step_k<STEP_PULL, true, true>(a, fs, fd, gs, gd, hp, s, tape_e, tape_m);
-        else step_k<STEP_PULL, false, true>(a, fs, fd, gs, gd, hp, s, tape_e, tape_m);
+        if (a.flow && coef<CT<P>>(a).darcy)
+            step_k<STEP_PULL, 2, true>(a, fs, fd, gs, gd, hp, s, tape_e, tape_m);
+        else if (a.flow)
+            step_k<STEP_PULL, 1, true>(a, fs, fd, gs, gd, hp, s, tape_e, tape_m);
+        else
+            step_k<STEP_PULL, 0, true>(a, fs, fd, gs, gd, hp, s, tape_e, tape_m);
     }
     static void adj_seed(const Args& a, const void* gs, const double* hp, void* lam,
                          double* Lpart, double* Jpart, cudaStream_t s) {

@@ -38,7 +38,7 @@ def test_library_builds_and_exports_every_declared_symbol():
 def test_param_block_layout_matches():
     L = B.lib()
     assert L.lbpc_params_size() == C.sizeof(B.LbpcParams)
-    assert L.lbpc_abi_version() == 2
+    assert L.lbpc_abi_version() == 3
 
 
 @pytest.mark.parametrize("precision,streaming,flow,per_node", [

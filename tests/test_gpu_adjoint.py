@@ -32,9 +32,11 @@ def _tiny(flow_model, enth_model, precision=inp.FP64):
     return shape, p, h0, Tw
 
 
-@pytest.mark.parametrize("flow_model,enth_model", [(1, 1), (2, 2), (1, 2), (0, 1), (0, 2)])
-def test_adjoint_equals_oracle_adjoint(flow_model, enth_model):
+@pytest.mark.parametrize("flow_model,enth_model,darcy_A", [
+    (1, 1, 0.0), (2, 2, 0.0), (1, 2, 0.0), (0, 1, 0.0), (0, 2, 0.0), (1, 1, 5.0)])
+def test_adjoint_equals_oracle_adjoint(flow_model, enth_model, darcy_A):
     shape, p, h0, Tw = _tiny(flow_model, enth_model)
+    p = p.replace(darcy_A=darcy_A)
     g = LBPC(shape, p)
     g.set_wall_temperature(0, Tw)
     g.set_initial_h(h0)

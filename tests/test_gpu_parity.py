@@ -86,6 +86,42 @@ def test_cavity_fp64(flow_model, enth_model, streaming):
     assert np.abs(o.fields()["u"]).max() > 1e-4  # the flow was active
 
 
+# the enthalpy-porosity solid drag in place of the liquid-fraction closure
+@pytest.mark.parametrize("precision,streaming,tol", [
+    (inp.FP64, inp.PULL, 1e-11), (inp.FP64, inp.AA, 1e-11), (inp.FP32, inp.PULL, 2e-4),
+    (inp.FP32, inp.AA, 2e-4)])
+def test_cavity_darcy_closure(precision, streaming, tol):
+    shape = (14, 7, 9)  # even n_x: the paired kernels take the interior rows
+    p = inp.Params(flow_model=inp.FLOW_MRT, precision=precision, streaming=streaming, Ra=3e4,
+                   Pr=0.7, St=0.8, darcy_A=5.0)
+    h0 = np.random.default_rng(1).uniform(-0.3, 2.0, int(np.prod(shape)))
+    g, o = _pair(shape, p, h0=h0)
+    g.step(61)
+    o.step(61)
+    err = _maxerr(_np(g.fields()), o.fields())
+    assert max(err.values()) <= tol, err
+    assert np.abs(o.fields()["u"]).max() > 1e-4
+
+
+@pytest.mark.parametrize("darcy_A,fl0", [(0.0, 0.3), (1.0, 0.3), (50.0, 0.9)])
+def test_steady_drag_velocity_on_gpu(darcy_A, fl0):
+    """The closed-form fixed point of the solid closures (see the oracle pin): uniform mushy
+    periodic box, u_z = phi G / (2 (1 - phi)), in FP64 and FP32 storage."""
+    for precision, tol in ((inp.FP64, 1e-12), (inp.FP32, 1e-4)):
+        p = inp.Params(flow_model=inp.FLOW_MRT, precision=precision, bc=[inp.PERIODIC] * 6,
+                       Ra=1e5, Pr=0.7, St=1.0, darcy_A=darcy_A)
+        g = LBPC((8, 5, 4), p)
+        g.set_initial_h(np.full(160, fl0 * g.lattice()["latent"]))
+        g.step(300)
+        G = g.lattice()["gbeta"] * (0.0 - p.Tref)
+        if darcy_A > 0:
+            uz = G / (darcy_A * (1 - fl0) ** 2 / (fl0 ** 3 + 1e-3))
+        else:
+            uz = fl0 * G / (2 * (1 - fl0))
+        u = _np(g.fields())["u"]
+        assert np.abs(u[2] - uz).max() <= tol * abs(uz), precision
+
+
 @pytest.mark.parametrize("bc", [
     [inp.PERIODIC] * 6,
     [inp.ADIABATIC] * 6,

@@ -8,6 +8,10 @@
   rows and melts monotonically.
 * Sec. 3.3 trends: at fixed Pr the melting is faster at larger Ra, and at fixed Ra faster at
   larger Pr (the paper's Fig. 12 observations), on small cavities.
+* The relaxation-rule study (Sec. 3.1.1 SRT vs MRT at tau = 0.564 / 6.9; Sec. 3.1.2 cases
+  (c)/(d)): FP64 GPU mode equals the oracle, FP32 reproduces its front positions.
+* Quasi-2D convective melting (Sec. 3.2.2, 64 x 1 x 64, to Fo = 20): conduction limit at
+  Fo = 4, convective bending later; a short FP32 run tracks the FP64 oracle.
 * Sec. 3.1.2 case (b) (per-phase C_p and conductivity, rates per node from f_l): FP64 GPU
   mode equals the oracle; FP32 and FP16 track it; the front follows Eq. 63 as in the
   oracle's own check.
@@ -121,3 +125,57 @@ def test_stefan_solidification_case_b_on_gpu():
     o.set_initial_h(h0)
     o.step(20000)
     assert np.abs(g.fields_host(mask=1)["T"] - o.fields()["T"]).max() < 1e-4
+
+
+@pytest.mark.parametrize("case", ["srt-0.564", "srt-6.9", "mrt-6.9", "rule", "c", "d"])
+def test_relaxation_rule_study_on_gpu(case):
+    if case.startswith(("srt", "mrt")):
+        tau = float(case.split("-")[1])
+        em = inp.ENTH_SRT if case.startswith("srt") else inp.ENTH_MRT
+        w = inp.stefan_melting(nx=96, enth_model=em, tau_g=tau)
+        steps = 20000 if tau < 1 else 1500
+    else:
+        chi = (1 / 1.14 - 0.5) * 0.25
+        w = inp.stefan_solidification(nx=96, ny=4, nz=4, chi=chi)
+        w.params = w.params.replace(sigma4={"rule": 0.0, "c": 1.9, "d": 0.1}[case])
+        steps = 20000
+    h0 = inp.h0_field(w)
+    o = oracle.Oracle(w.shape, w.params)
+    o.set_initial_h(h0)
+    o.step(steps)
+    Fo = o.fields()
+    for prec, tol in ((inp.FP64, 1e-9), (inp.FP32, 2e-3)):
+        g = LBPC(w.shape, w.params.replace(precision=prec))
+        g.set_initial_h(h0)
+        g.step(steps)
+        Fg = g.fields_host(mask=1 | 2)
+        assert np.abs(Fg["fl"] - Fo["fl"]).sum() <= tol * w.nodes, (prec, case)
+        assert np.abs(Fg["T"] - Fo["T"]).max() <= (1e-9 if prec == inp.FP64 else 1e-3)
+
+
+def test_quasi_2d_convective_melting_on_gpu():
+    w = inp.cavity_melting_2d(n=64, precision=inp.FP32)
+    h0 = inp.h0_field(w)
+    o = oracle.Oracle((32, 1, 32), inp.cavity_melting_2d(n=32).params)
+    o.set_initial_h(inp.h0_field(inp.cavity_melting_2d(n=32)))
+    o.step(3000)
+    g32 = LBPC((32, 1, 32), inp.cavity_melting_2d(n=32).params)
+    g32.set_initial_h(inp.h0_field(inp.cavity_melting_2d(n=32)))
+    g32.step(3000)
+    assert np.abs(g32.fields_host(mask=1)["T"] - o.fields()["T"]).max() < 1e-4
+    g = LBPC(w.shape, w.params)
+    g.set_initial_h(h0)
+    chi = g.lattice()["chi"]
+    k = nm.melting_k(0.01)
+    n = w.shape[0]
+    depths = {}
+    for Fo in (4, 10, 20):
+        g.step(int(round(Fo * n * n / chi)) - g.step_count)
+        depth = g.fields_host(mask=2)["fl"][:, 0, :].sum(axis=1) / n
+        depths[Fo] = depth
+        X = 2 * k * np.sqrt(Fo)
+        if Fo == 4:
+            assert abs(depth.mean() - X) / X < 0.01 and depth[-1] - depth[0] < 0.03
+        else:
+            assert depth.mean() > X and depth[-1] - depth[0] > 0.05
+    assert depths[20][-1] - depths[20][0] > depths[10][-1] - depths[10][0]

@@ -6,6 +6,8 @@
   J = sum f_l(h_N) computed by the oracle's forward run (initial state held fixed,
   as the adjoint defines it).
 * Dot-product consistency: dJ/dT_w . v equals the directional finite difference.
+* All of it also with the enthalpy-porosity solid drag in place of the liquid-fraction
+  closure.
 """
 import numpy as np
 import pytest
@@ -21,11 +23,13 @@ def _rand_node(o, rng, h, flow):
     return f, g
 
 
-@pytest.mark.parametrize("flow_model,enth_model", [(1, 1), (2, 2), (0, 1), (0, 2)])
+@pytest.mark.parametrize("flow_model,enth_model,darcy_A", [(1, 1, 0.0), (2, 2, 0.0), (0, 1, 0.0),
+                                                          (0, 2, 0.0), (1, 1, 5.0)])
 @pytest.mark.parametrize("branch", ["solid", "mushy", "liquid"])
-def test_complex_step_jacobian_matches_finite_differences(flow_model, enth_model, branch):
+def test_complex_step_jacobian_matches_finite_differences(flow_model, enth_model, darcy_A,
+                                                          branch):
     p = inp.Params(flow_model=flow_model, enth_model=enth_model, Ra=3e4, Pr=0.7, St=0.8,
-                   tau_g=0.0 if flow_model else 0.9, Cp_l=1.3)
+                   tau_g=0.0 if flow_model else 0.9, Cp_l=1.3, darcy_A=darcy_A)
     o = oracle.Oracle((1, 1, 1), p, alloc=False)
     L = o.lattice()["latent"]
     h = {"solid": -0.3, "mushy": 0.4 * L, "liquid": L + 0.5}[branch]
@@ -59,10 +63,10 @@ def test_complex_step_jacobian_matches_finite_differences(flow_model, enth_model
     assert np.abs((outs[0] - outs[1]) / (2 * dSt) - dL * dLdSt).max() <= 1e-6
 
 
-def _cavity(flow_model=1, enth_model=1):
+def _cavity(flow_model=1, enth_model=1, darcy_A=0.0):
     shape = (6, 5, 4)
     p = inp.Params(flow_model=flow_model, enth_model=enth_model, precision=inp.FP64, Ra=2e4,
-                   Pr=0.7, St=0.8, tau_g=0.0 if flow_model else 0.9)
+                   Pr=0.7, St=0.8, tau_g=0.0 if flow_model else 0.9, darcy_A=darcy_A)
     h0 = np.random.default_rng(3).uniform(-0.3, 1.6, int(np.prod(shape)))
     Tw = inp.wall_temperature_field(shape[1], shape[2], seed=1)
     o = oracle.Oracle(shape, p)
@@ -80,9 +84,10 @@ def _J(shape, p, Tw, f0, g0, steps):
     return o.fields()["fl"].sum()
 
 
-@pytest.mark.parametrize("flow_model,enth_model", [(1, 1), (2, 2), (0, 1)])
-def test_adjoint_gradients_match_finite_differences(flow_model, enth_model):
-    shape, p, Tw, f0, g0 = _cavity(flow_model, enth_model)
+@pytest.mark.parametrize("flow_model,enth_model,darcy_A", [(1, 1, 0.0), (2, 2, 0.0), (0, 1, 0.0),
+                                                          (1, 1, 5.0)])
+def test_adjoint_gradients_match_finite_differences(flow_model, enth_model, darcy_A):
+    shape, p, Tw, f0, g0 = _cavity(flow_model, enth_model, darcy_A)
     steps = 25
     o = oracle.Oracle(shape, p)
     o.set_wall_temperature(0, Tw)

@@ -7,6 +7,10 @@
   diffusivity fixed by the relaxation time.
 * Eq. 47 (Sec. 2.4): with sigma_1 + sigma_4 = 2 the solid ahead of the front stays
   exactly at h_m; otherwise it does not; SRT with tau far from 1 cools the solid.
+* The relaxation-time study of Sec. 3.1.1 (SRT vs MRT at tau = 0.564, 1.012, 6.9) and the
+  rule-breaking cases (c)/(d) of Sec. 3.1.2, as the paper describes them.
+* Quasi-2D convective melting (Sec. 3.2.2): the conduction limit at early Fo (Eq. 61) and
+  the convective bending of the interface later.
 * Steady conduction between isothermal walls gives Nu = 1.
 """
 import math
@@ -193,6 +197,93 @@ def test_srt_far_from_unit_tau_cools_the_solid():
     w1 = inp.stefan_melting(enth_model=inp.ENTH_SRT, tau_g=1.0)
     err1, _ = _solid_ahead_error(w1, 3000)
     assert err1 <= 1e-13
+
+
+def _melting_errors(enth_model, tau, steps, nx=96):
+    """Front and temperature errors of Stefan melting (St = 0.1) against Eq. 60-61."""
+    w = inp.stefan_melting(nx=nx, enth_model=enth_model, tau_g=tau)
+    o = oracle.Oracle(w.shape, w.params)
+    o.set_initial_h(inp.h0_field(w))
+    o.step(steps)
+    chi = o.lattice()["chi"]
+    k = nm.melting_k(0.1)
+    F = o.fields()
+    T, fl = F["T"][0, 0, :], F["fl"][0, 0, :]
+    x = np.arange(nx) + 0.5
+    X = float(nm.melting_front(steps, chi, k))
+    Ta = nm.melting_temperature(x, steps, chi, k)
+    return (fl.sum() - X) / X, np.abs(T - Ta).max(), T[x > X + 2].min()
+
+
+def test_srt_versus_mrt_over_the_relaxation_time():
+    """Sec. 3.1.1 relaxation-time study (tau = 0.564, 1.012, 6.9): MRT follows Eq. 60-61 at
+    every tau; SRT only near tau = 1 -- at 0.564 it cools the solid below T_m and lags, at
+    6.9 it deviates at the interface."""
+    for tau, steps in ((0.564, 20000), (1.012, 5000), (6.9, 1500)):
+        ef_m, eT_m, Tmin_m = _melting_errors(inp.ENTH_MRT, tau, steps)
+        ef_s, eT_s, Tmin_s = _melting_errors(inp.ENTH_SRT, tau, steps)
+        assert abs(ef_m) < 5e-3 and abs(Tmin_m) < 1e-9
+        if tau == 1.012:
+            assert abs(ef_s) < 5e-3 and abs(Tmin_s) < 1e-6
+        else:
+            assert abs(ef_s) > 0.02
+        if tau == 0.564:
+            assert Tmin_s < -1e-3
+        if tau == 6.9:
+            assert eT_s > 0.1 and eT_m < 0.01
+
+
+def _solidification_rule(sigma4, chi, t=20000, nx=96):
+    w = inp.stefan_solidification(nx=nx, chi=chi)
+    o = oracle.Oracle(w.shape, w.params.replace(sigma4=sigma4))
+    o.set_initial_h(inp.h0_field(w))
+    o.step(t)
+    F = o.fields()
+    T, fl = F["T"][0, 0, :], F["fl"][0, 0, :]
+    k = nm.solidification_k(0.004, 0.004, chi, chi)
+    x = np.arange(nx) + 0.5
+    X = float(nm.solidification_front(t, chi, k))
+    Ta = nm.solidification_temperature(x, t, chi, chi, k)
+    liquid = (x > X + 1) & (x < X + 30)
+    mushy = int(((fl > 1e-6) & (fl < 1 - 1e-6)).sum())
+    return ((1 - fl).sum() - X) / X, np.abs(T[liquid] - Ta[liquid]).max(), mushy
+
+
+def test_relaxation_rule_cases_c_and_d():
+    """Sec. 3.1.2 cases (c)/(d): case (a) physics with sigma_1..3 = 1.14 and sigma_4..6 =
+    2 - sigma_1 (Eq. 47), 1.9 (c) or 0.1 (d).  Breaking the rule moves the front and puts
+    an error into the liquid ahead of it that the rule keeps out; (d) also widens the
+    interface beyond one node."""
+    chi = (1 / 1.14 - 0.5) * 0.25
+    ef_r, eT_r, w_r = _solidification_rule(0.0, chi)
+    ef_c, eT_c, w_c = _solidification_rule(1.9, chi)
+    ef_d, eT_d, w_d = _solidification_rule(0.1, chi)
+    assert abs(ef_r) < 0.02 and eT_r < 0.015 and w_r <= 1
+    assert abs(ef_c) > 0.04 and eT_c > 3 * eT_r
+    assert abs(ef_d) > 0.1 and eT_d > 3 * eT_r and w_d >= 3
+
+
+def test_quasi_2d_convective_melting():
+    """Sec. 3.2.2 (Table 1: Ra 2.5e4, Pr 0.02, Ste 0.01), 32 x 1 x 32: at Fo = 4 conduction
+    dominates -- the melt depth equals the 1D Neumann value 2 k sqrt(Fo) (Eq. 61) and the
+    interface is nearly vertical; by Fo = 10 convection bends it (more melt at the top, where
+    the heated liquid rises) and melting runs ahead of pure conduction."""
+    w = inp.cavity_melting_2d(n=32, precision=inp.FP64)
+    o = oracle.Oracle(w.shape, w.params)
+    o.set_initial_h(inp.h0_field(w))
+    chi = o.lattice()["chi"]
+    k = nm.melting_k(0.01)
+    n, done = w.shape[0], 0
+    for Fo in (4, 10):
+        t = int(round(Fo * n * n / chi))
+        o.step(t - done)
+        done = t
+        depth = o.fields()["fl"][:, 0, :].sum(axis=1) / n  # per z row, in cavity widths
+        X = 2 * k * math.sqrt(Fo)
+        if Fo == 4:
+            assert abs(depth.mean() - X) / X < 0.01 and depth[-1] - depth[0] < 0.03
+        else:
+            assert depth.mean() > X and depth[-1] - depth[0] > 0.05
 
 
 @pytest.mark.parametrize("enth_model", [inp.ENTH_SRT, inp.ENTH_MRT])

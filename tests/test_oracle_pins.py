@@ -250,3 +250,27 @@ def test_mirror_symmetry_in_y():
     assert np.abs(u[1] + u[1][:, ::-1, :]).max() <= 1e-12
     assert np.abs(u[2] - u[2][:, ::-1, :]).max() <= 1e-12
     assert np.abs(u).max() > 1e-5
+
+
+@pytest.mark.parametrize("darcy_A,fl0", [(0.0, 0.3), (0.0, 0.9), (1.0, 0.3), (50.0, 0.9)])
+def test_solid_closures_reach_the_steady_drag_velocity(darcy_A, fl0):
+    """Uniform mushy periodic box at T_m: buoyancy is a uniform body force G = g beta (T_m -
+    T_ref) along z, and each step adds F = G + F_s to the momentum.  With u = phi u* and F_s =
+    -2 (1 - phi) u* the fixed point is u* = G / (2 (1 - phi)), u_z = phi G / (2 (1 - phi)):
+    phi = f_l for the liquid-fraction closure (Sec. 3.3 reading), and for the enthalpy-porosity
+    drag phi = 1 / (1 + D/2), D = A (1 - f_l)^2 / (f_l^3 + 1e-3), i.e. u_z = G / D."""
+    p = inp.Params(flow_model=inp.FLOW_MRT, precision=inp.FP64, bc=[inp.PERIODIC] * 6,
+                   Ra=1e5, Pr=0.7, St=1.0, darcy_A=darcy_A)
+    o = oracle.Oracle((6, 5, 4), p)
+    o.set_initial_h(np.full(o.N, fl0 * o.lattice()["latent"]))
+    o.step(300)
+    F = o.fields()
+    G = o.lattice()["gbeta"] * (0.0 - p.Tref)
+    if darcy_A > 0:
+        D = darcy_A * (1 - fl0) ** 2 / (fl0 ** 3 + 1e-3)
+        uz = G / D
+    else:
+        uz = fl0 * G / (2 * (1 - fl0))
+    assert np.abs(F["u"][2] - uz).max() <= 1e-12 * abs(uz)
+    assert np.abs(F["u"][:2]).max() <= 1e-15
+    assert np.abs(F["fl"] - fl0).max() == 0.0
