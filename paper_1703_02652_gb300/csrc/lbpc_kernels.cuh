@@ -840,8 +840,9 @@ LBPC_HD void step_pair_pull(const Args& a, int x0, int y, int z, const TF<P>* fs
 }
 
 
-// Hides v's value from the compiler: the scatter addresses of the odd AA step equal gather
-// addresses, and without this the compiler keeps them all live across the collision.
+// Hides v's value from the compiler: the scatter addresses of an AA step are gather
+// addresses (the same slots, in place), and without this the compiler keeps them all live
+// across the collision.
 template <class T>
 LBPC_HD void opaque(T& v) {
 #if defined(__CUDA_ARCH__)
@@ -933,9 +934,7 @@ LBPC_HD void step_pair_aa(const Args& a, int x0, int y, int z, TF<P>* F, TG<P>* 
     int m0 = n0, mdn = dn0, mup = up1, tsy = sy, tsz = sz;
     TF<P>* Fw = F;
     TG<P>* Gw = G;
-    if constexpr (ODD) {
-        opaque(m0); opaque(mdn); opaque(mup); opaque(tsy); opaque(tsz); opaque(Fw); opaque(Gw);
-    }
+    opaque(m0); opaque(mdn); opaque(mup); opaque(tsy); opaque(tsz); opaque(Fw); opaque(Gw);
     // ---- scatter ----
     if constexpr (FLOW) {
 #define LBPC_ASF(q, ex, ey, ez, op)                                                      \
@@ -1558,8 +1557,9 @@ k_step_pull_x2(const __grid_constant__ Args a, const TF<P>* fs,
 
 
 // AA step, two nodes per thread along x (even nx); same vote as the pull pair kernel.
+// Five blocks per SM (96 registers; a few bytes of spills in some variants).
 template <int P, int FLOW, bool ODD>
-__global__ void __launch_bounds__(STEP_THREADS, 4)
+__global__ void __launch_bounds__(STEP_THREADS, 5)
 k_step_aa_x2(const __grid_constant__ Args a, TF<P>* F, TG<P>* G, double* __restrict__ hp) {
     const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
