@@ -333,7 +333,10 @@ def run_ours(args):
                    "precision": inp.PRECISION_NAMES[precision],
                    "streaming": "aa" if streaming == inp.AA else "pull",
                    "report_every": p.report_every,
-                   "l2": "working set > 129 MB L2 (no flush needed)",
+                   "l2": (f"working set {w.nodes * bpl / 1e6:.0f} MB > 129 MB L2 (no flush needed)"
+                          if w.nodes * bpl > 129e6 else
+                          f"working set {w.nodes * bpl / 1e6:.0f} MB fits in the 129 MB L2 "
+                          "(small-lattice case, not an HBM measurement)"),
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_kind,
