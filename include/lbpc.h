@@ -166,8 +166,9 @@ lbpc_status lbpc_set_initial_h(lbpc_handle *h, const double *h_host);
 lbpc_status lbpc_set_wall_temperature(lbpc_handle *h, int face, const double *T_host);
 
 /* Advance n >= 0 time steps on the handle's stream (asynchronous unless report_every
- * > 0, in which case the call waits for the stream and returns LBPC_ERR_DIVERGED if the
- * last recorded diagnostics saw a non-finite value).  LBPC_ERR_STATE after divergence. */
+ * > 0 and the call passes a diagnostics point, in which case the call waits for the stream
+ * and returns LBPC_ERR_DIVERGED if the last diagnostics it recorded saw a non-finite
+ * value).  LBPC_ERR_STATE after divergence. */
 lbpc_status lbpc_step(lbpc_handle *h, int n);
 
 /* Macroscopic fields of the current state (after the last stream, Eq. 2 / Eq. 56),

@@ -140,6 +140,19 @@ def cavity_melting(n=64, Ra=1e5, Pr=0.02, St=1.0, precision=FP32, streaming=PULL
     return Workload(name, shape, p, steps, seed=0, perturb=1e-6)
 
 
+def corner_solidification(n=128, chi=0.1, precision=FP64) -> Workload:
+    """2D solidification in a corner (Sec. 3.2.1): liquid at T_0 = 0.3 in x, z > 0, the
+    planes x = -1/2 and z = -1/2 held at T_1 = -1 from t = 0, T_f = 0; equal properties,
+    Ste_s = C_p (T_f - T_1) / L = 4 (L = 1/4, so St = C_p (T_0 - T_f) / L = 1.2); one
+    periodic node along y, adiabatic far faces; conduction only with chi given."""
+    L = 0.25
+    p = Params(flow_model=FLOW_NONE, enth_model=ENTH_MRT, precision=precision,
+               bc=[ISOTHERMAL, ADIABATIC, PERIODIC, PERIODIC, ISOTHERMAL, ADIABATIC],
+               T_wall=[-1.0, 0.0, 0.0, 0.0, -1.0, 0.0], St=0.3 / L, Th=0.3, Tm=0.0,
+               tau_g=chi / 0.25 + 0.5, h0=L + 0.3)
+    return Workload(f"corner-solidification-{n}x1x{n}", (n, 1, n), p, 4500)
+
+
 def cavity_melting_2d(n=64, Ra=2.5e4, Pr=0.02, St=0.01, precision=FP32, steps=100000,
                       report_every=0) -> Workload:
     """Quasi-2D convective melting (Sec. 3.2.2, Table 1): a 1 x 1 cavity in x-z, infinite

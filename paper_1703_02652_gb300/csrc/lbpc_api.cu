@@ -246,6 +246,8 @@ lbpc_status reset_from_h(lbpc_handle* h, const double* h_host) {
     h->step = 0;
     h->hist_count = 0;
     h->diverged = false;
+    // no diagnostics recorded yet (the workspace comes uninitialised from the caller)
+    LBPC_CK(h, cudaMemsetAsync(h->result, 0, sizeof(double) * LBPC_S_COUNT, h->stream));
     lbpc_status s = init_state(h, nullptr, nullptr, h->stage);
     if (s != LBPC_OK) return s;
     LBPC_CK(h, cudaStreamSynchronize(h->stream));
@@ -363,6 +365,7 @@ lbpc_status lbpc_step(lbpc_handle* h, int n) {
     lbpc_status s = set_device(h);
     if (s != LBPC_OK) return s;
     const int rep = h->p.report_every;
+    bool recorded = false;  // diagnostics taken during this call
     for (int i = 0; i < n; i++) {
         if (h->p.streaming == LBPC_PULL) {
             h->L->step(h->args, STEP_PULL, h->f[h->cur], h->f[1 - h->cur], h->g[h->cur],
@@ -377,10 +380,11 @@ lbpc_status lbpc_step(lbpc_handle* h, int n) {
         if (rep > 0 && h->step % rep == 0) {
             s = diagnostics(h, true);
             if (s != LBPC_OK) return s;
+            recorded = true;
         }
     }
     LBPC_CK(h, cudaGetLastError());
-    if (rep > 0 && n > 0) {
+    if (recorded) {
         double nan = 0.0;
         LBPC_CK(h, cudaMemcpyAsync(&nan, h->result + LBPC_S_NAN, sizeof(double),
                                    cudaMemcpyDeviceToHost, h->stream));

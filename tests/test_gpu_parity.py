@@ -122,6 +122,27 @@ def test_steady_drag_velocity_on_gpu(darcy_A, fl0):
         assert np.abs(u[2] - uz).max() <= tol * abs(uz), precision
 
 
+@pytest.mark.parametrize("streaming", [inp.PULL, inp.AA])
+def test_short_steps_before_the_first_diagnostics(streaming):
+    """With report_every > 0, calls that end before the first diagnostics point report no
+    divergence (nothing recorded yet) and equal stepping in one call."""
+    shape = (24, 12, 10)
+    p = inp.Params(precision=inp.FP32, streaming=streaming, Ra=1e5, Pr=0.7, St=1.0,
+                   report_every=10)
+    h0 = np.random.default_rng(2).uniform(-0.3, 1.8, int(np.prod(shape)))
+    a, b = LBPC(shape, p), LBPC(shape, p)
+    a.set_initial_h(h0)
+    b.set_initial_h(h0)
+    a.step(23)
+    for _ in range(23):
+        b.step(1)
+    assert a.step_count == b.step_count == 23
+    Fa, Fb = _np(a.fields()), _np(b.fields())
+    for k in KEYS:
+        assert np.array_equal(Fa[k], Fb[k]), k
+    assert np.array_equal(a.history(), b.history())
+
+
 @pytest.mark.parametrize("bc", [
     [inp.PERIODIC] * 6,
     [inp.ADIABATIC] * 6,

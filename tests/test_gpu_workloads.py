@@ -12,6 +12,8 @@
   (c)/(d)): FP64 GPU mode equals the oracle, FP32 reproduces its front positions.
 * Quasi-2D convective melting (Sec. 3.2.2, 64 x 1 x 64, to Fo = 20): conduction limit at
   Fo = 4, convective bending later; a short FP32 run tracks the FP64 oracle.
+* 2D corner solidification (Sec. 3.2.1, 128 x 1 x 128): FP64 GPU mode equals the oracle,
+  FP32 tracks it, and the corner stays symmetric about the diagonal.
 * Sec. 3.1.2 case (b) (per-phase C_p and conductivity, rates per node from f_l): FP64 GPU
   mode equals the oracle; FP32 and FP16 track it; the front follows Eq. 63 as in the
   oracle's own check.
@@ -179,3 +181,20 @@ def test_quasi_2d_convective_melting_on_gpu():
         else:
             assert depth.mean() > X and depth[-1] - depth[0] > 0.05
     assert depths[20][-1] - depths[20][0] > depths[10][-1] - depths[10][0]
+
+
+@pytest.mark.parametrize("precision,streaming,tol", [
+    (inp.FP64, inp.PULL, 1e-9), (inp.FP64, inp.AA, 1e-9), (inp.FP32, inp.PULL, 1e-4)])
+def test_corner_solidification_on_gpu(precision, streaming, tol):
+    w = inp.corner_solidification(n=128, precision=precision)
+    p = w.params.replace(streaming=streaming)
+    h0 = inp.h0_field(w)
+    g = LBPC(w.shape, p)
+    g.set_initial_h(h0)
+    g.step(w.steps)
+    o = oracle.Oracle(w.shape, p.replace(precision=inp.FP64, streaming=inp.PULL))
+    o.set_initial_h(h0)
+    o.step(w.steps)
+    T = g.fields_host(mask=1)["T"][:, 0, :]
+    assert np.abs(T - o.fields()["T"][:, 0, :]).max() <= tol
+    assert np.abs(T - T.T).max() <= (1e-12 if precision == inp.FP64 else 1e-5)

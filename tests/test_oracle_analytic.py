@@ -11,6 +11,8 @@
   rule-breaking cases (c)/(d) of Sec. 3.1.2, as the paper describes them.
 * Quasi-2D convective melting (Sec. 3.2.2): the conduction limit at early Fo (Eq. 61) and
   the convective bending of the interface later.
+* 2D corner solidification (Sec. 3.2.1): diagonal symmetry, the 1D Neumann limit far from
+  the corner, self-similar corner enhancement.
 * Steady conduction between isothermal walls gives Nu = 1.
 """
 import math
@@ -284,6 +286,35 @@ def test_quasi_2d_convective_melting():
             assert abs(depth.mean() - X) / X < 0.01 and depth[-1] - depth[0] < 0.03
         else:
             assert depth.mean() > X and depth[-1] - depth[0] > 0.05
+
+
+def test_corner_solidification():
+    """Sec. 3.2.1 set-up (comparison data not in the container, so checked against what must
+    hold): the field is symmetric about the diagonal; far from the corner the front and the
+    temperature follow the 1D Neumann solution of Eq. 62-63 (Ste_s = 4, Ste_l = 1.2, equal
+    chi); the corner, cooled from two sides, freezes further, by a depth ratio that stays
+    constant in time (the problem is self-similar)."""
+    w = inp.corner_solidification(n=128)
+    o = oracle.Oracle(w.shape, w.params)
+    o.set_initial_h(inp.h0_field(w))
+    chi = 0.1
+    k = nm.solidification_k(4.0, 1.2, chi, chi)
+    x = np.arange(w.shape[0]) + 0.5
+    ratios = []
+    done = 0
+    for t in (1125, 4500):
+        o.step(t - done)
+        done = t
+        F = o.fields()
+        fl, T = F["fl"][:, 0, :], F["T"][:, 0, :]  # (z, x)
+        assert np.abs(T - T.T).max() < 1e-13
+        X = float(nm.solidification_front(t, chi, k))
+        far = (1.0 - fl[:, -1]).sum()  # depth along z at the far (mirror) column
+        assert abs(far - X) <= max(0.03 * X, 0.6)
+        Ta = nm.solidification_temperature(x, t, chi, chi, k, T0=0.3, T1=-1.0)
+        assert np.abs(T[:, -1] - Ta).max() < 0.01
+        ratios.append((1.0 - np.diag(fl)).sum() / X)
+    assert ratios[0] > 1.1 and abs(ratios[1] / ratios[0] - 1) < 0.03
 
 
 @pytest.mark.parametrize("enth_model", [inp.ENTH_SRT, inp.ENTH_MRT])
