@@ -46,10 +46,10 @@ def _peaks():
 
 
 def _kernel_hash():
-    """Hash of the sources that define the step kernels (device code, its headers and the
-    coefficient set-up); host API code is left out."""
+    """Hash of the sources that define the step kernels (device code and its headers);
+    host API code is left out."""
     csrc = os.path.join(ROOT, "paper_1703_02652_gb300", "csrc")
-    files = [os.path.join(csrc, n) for n in ("lbpc_kernels.cuh", "lbpc_internal.h", "lbpc_host.h")]
+    files = [os.path.join(csrc, n) for n in ("lbpc_kernels.cuh", "lbpc_internal.h")]
     files += sorted(glob.glob(os.path.join(csrc, "lbpc_kern_*.cu")))
     h = hashlib.sha256()
     for p in files:

@@ -146,8 +146,9 @@ size_t lbpc_workspace_bytes(int nx, int ny, int nz, const lbpc_params *p);
  * aligned, >= lbpc_workspace_bytes) and initialise the equilibrium state at uniform
  * h0 and uniform wall temperatures.  cuda_stream is a cudaStream_t (NULL: legacy
  * default stream) used for every later launch.  On success *out owns no memory but
- * the handle itself; dev_ws must outlive it.  Errors: LBPC_ERR_PARAM (before any CUDA
- * call), LBPC_ERR_WORKSPACE, LBPC_ERR_CUDA. */
+ * the handle itself; dev_ws must outlive it.  Sizes: nx ny nz < 2^31 nodes, ny and nz
+ * <= 65535 (grid limits).  Errors: LBPC_ERR_PARAM (before any CUDA call),
+ * LBPC_ERR_WORKSPACE, LBPC_ERR_CUDA. */
 lbpc_status lbpc_create(int nx, int ny, int nz, const lbpc_params *p, void *dev_ws,
                         size_t ws_bytes, void *cuda_stream, lbpc_handle **out);
 

@@ -83,7 +83,10 @@ __global__ void __launch_bounds__(256) k_sum(const double* __restrict__ p, int n
 }
 
 __global__ void k_fill(double* p, double v, int n) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = v;
+    // 64-bit index: i + stride may pass 2^31 - 1 for n near the 2^31 - 1 node limit
+    for (long long i = blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        p[i] = v;
 }
 
 // Deterministic second stage of the diagnostics: fixed-order sums of the block

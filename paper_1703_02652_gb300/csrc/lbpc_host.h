@@ -20,6 +20,8 @@ inline bool validate_and_map(int nx, int ny, int nz, const lbpc_params* p, Deriv
     if (!p) { e = "null parameter block"; return false; }
     if (nx < 1 || ny < 1 || nz < 1) { e = "lattice extents must be >= 1"; return false; }
     if ((long long)nx * ny * nz >= (1LL << 31)) { e = "lattice exceeds 2^31 - 1 nodes"; return false; }
+    // the kernels map z to gridDim.z and y to gridDim.y (at most 65535 blocks each)
+    if (ny > 65535 || nz > 65535) { e = "ny and nz must be <= 65535"; return false; }
     if (p->flow_model < LBPC_FLOW_NONE || p->flow_model > LBPC_FLOW_SRT) { e = "flow_model must be 0, 1 or 2"; return false; }
     if (p->enth_model != LBPC_ENTH_MRT && p->enth_model != LBPC_ENTH_SRT) { e = "enth_model must be 1 or 2"; return false; }
     if (p->precision < LBPC_FP64 || p->precision > LBPC_BF16S_G32) { e = "precision must be 0..5"; return false; }

@@ -1592,8 +1592,10 @@ k_macro(const __grid_constant__ Args a, const TF<P>* __restrict__ fs,
         const TG<P>* __restrict__ gs, const double* __restrict__ hp,
         const MacroOut out) {
     double acc[NRED] = {0, 0, 0, 0, 0, 0};
-    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < a.N; n += gridDim.x * blockDim.x)
-        macro_node<P, LAYOUT, FLOW>(a, n, fs, gs, hp, out, out.partial ? acc : nullptr);
+    // 64-bit loop index: n + stride may pass 2^31 - 1 near the node limit
+    for (long long n = blockIdx.x * blockDim.x + threadIdx.x; n < a.N;
+         n += (long long)gridDim.x * blockDim.x)
+        macro_node<P, LAYOUT, FLOW>(a, (int)n, fs, gs, hp, out, out.partial ? acc : nullptr);
     if (!out.partial) return;
     __shared__ double sh[RED_THREADS / 32][NRED];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;

@@ -86,6 +86,10 @@ def test_bad_extents_and_missing_workspace():
     assert L.lbpc_create(0, 8, 8, C.byref(cp), None, 0, None, C.byref(h)) == B.LBPC_ERR_PARAM
     assert L.lbpc_create(2048, 2048, 1024, C.byref(cp), None, 0, None,
                          C.byref(h)) == B.LBPC_ERR_PARAM
+    # grid limits: ny and nz at most 65535 (the node count alone would be fine)
+    assert L.lbpc_workspace_bytes(2, 2, 65536, C.byref(cp)) == 0
+    assert L.lbpc_workspace_bytes(2, 65536, 2, C.byref(cp)) == 0
+    assert L.lbpc_workspace_bytes(2, 2, 65535, C.byref(cp)) > 0
     st = L.lbpc_create(8, 8, 8, C.byref(cp), None, 0, None, C.byref(h))
     assert st == B.LBPC_ERR_WORKSPACE
     st = L.lbpc_create(8, 8, 8, C.byref(cp), C.c_void_p(256), 16, None, C.byref(h))

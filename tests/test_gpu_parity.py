@@ -377,3 +377,38 @@ def test_full_size_bench_configuration_sampled(precision, tol):
     assert np.abs(g1s - go).max() <= tol
     s = g.scalars()
     assert s["nan"] == 0 and s["liquid_vol"] > 0
+
+
+def test_lattice_above_the_pair_limit():
+    """A lattice of 1024 x 1024 x 684 = 717,225,984 nodes (above (2^31 - 1)/3, so the step runs
+    the one-node-per-thread kernels; FP16 storage with flow, 83 GB of workspace), periodic,
+    with an enthalpy that varies only along z: every (x, y) column must then evolve exactly
+    like the 1 x 1 x 684 oracle lattice, which any index error at this size would break."""
+    shape = (1024, 1024, 684)
+    nx, ny, nz = shape
+    p = inp.Params(flow_model=inp.FLOW_MRT, precision=inp.FP16, bc=[inp.PERIODIC] * 6, Ra=1e5,
+                   Pr=0.7, St=1.0, report_every=0)
+    o = oracle.Oracle((1, 1, nz), p)
+    L = o.lattice()["latent"]
+    z = np.arange(nz)
+    hz = L + 0.5 + 0.3 * np.sin(2 * np.pi * z / nz)  # liquid, T between 0.2 and 0.8
+    o.set_initial_h(hz)
+    o.step(3)
+    Tz = o.fields()["T"][:, 0, 0]
+    g = LBPC(shape, p)
+    g.set_initial_h(np.repeat(hz, nx * ny))
+    g.step(3)
+    F = g.fields()
+    T = F["T"]
+    del F
+    rng = np.random.default_rng(4)
+    xs = np.concatenate([[0, nx - 1], rng.integers(0, nx, 64)])
+    ys = np.concatenate([[0, ny - 1], rng.integers(0, ny, 64)])
+    for zz in (0, nz // 2, nz - 1):
+        plane = T[zz, :, :]
+        assert float((plane.max() - plane.min()).item()) < 1e-12  # uniform in x and y
+        assert abs(float(plane[ys[0], xs[0]].item()) - Tz[zz]) < 2e-3
+    Tc = T[:, ys[2], xs[2]].cpu().numpy()  # one column against the oracle
+    assert np.abs(Tc - Tz).max() < 2e-3
+    del T
+    assert g.scalars()["nan"] == 0
