@@ -652,7 +652,7 @@ AdjLayout adj_layout(const lbpc_handle* h, int nsteps, int k) {
     for (int f = 0; f < 6; f++) amax = std::max(amax, (size_t)face_area(h->nx, h->ny, h->nz, f));
     L.gtw = off; off = align_up(off + 8 * amax);
     L.nblocks = node_grid_blocks(h->nx, h->ny, h->nz);
-    L.Lpart = off; off = align_up(off + 8 * (size_t)L.nblocks);
+    L.Lpart = off; off = align_up(off + 8 * (size_t)L.nblocks * ADJ_WARPS_PER_BLOCK);
     L.Jpart = off; off = align_up(off + 8 * (size_t)L.nblocks);
     L.red = off; off = align_up(off + 8 * 4);
     L.total = off;
@@ -794,7 +794,7 @@ lbpc_status lbpc_adjoint_backward(lbpc_handle* h, int face, double* dJ_dTw_host,
         }
         h->launches += len;
     }
-    k_sum<<<1, 256, 0, h->stream>>>(A.Lpart, A.nblocks, A.red + 1);
+    k_sum<<<1, 256, 0, h->stream>>>(A.Lpart, A.nblocks * ADJ_WARPS_PER_BLOCK, A.red + 1);
     h->launches++;
     LBPC_CK(h, cudaGetLastError());
     s = restore_state(h, A.ckpt + (size_t)A.nseg * A.ckpt_bytes);  // back to the final state

@@ -160,6 +160,23 @@ inline void fill_coef(Coef<C>& c, const lbpc_params& p, const Derived& d) {
     const bool srt = p.enth_model == LBPC_ENTH_SRT;
     c.s4_a = (C)(srt ? 0.0 : (p.sigma4 > 0 ? p.sigma4 : 2.0));
     c.s4_b = (C)(srt ? 1.0 : (p.sigma4 > 0 ? 0.0 : -1.0));
+    c.j_s_e = (C)(d.s_e / 2394.0);
+    c.j_h_e = (C)((1.0 - 0.5 * d.s_e) / 2394.0);
+    c.j_s_eps = (C)(d.s_eps / 252.0);
+    c.j_h_eps = (C)((1.0 - 0.5 * d.s_eps) / 252.0);
+    c.j_s_q = (C)(d.s_q / 40.0);
+    c.j_h_q = (C)((1.0 - 0.5 * d.s_q) / 40.0);
+    c.j_s_nu9 = (C)(d.s_nu / 36.0);
+    c.j_h_nu9 = (C)((1.0 - 0.5 * d.s_nu) / 36.0);
+    c.j_s_pi10 = (C)(d.s_pi / 72.0);
+    c.j_h_pi10 = (C)((1.0 - 0.5 * d.s_pi) / 72.0);
+    c.j_s_nu11 = (C)(d.s_nu / 12.0);
+    c.j_h_nu11 = (C)((1.0 - 0.5 * d.s_nu) / 12.0);
+    c.j_s_pi12 = (C)(d.s_pi / 24.0);
+    c.j_h_pi12 = (C)((1.0 - 0.5 * d.s_pi) / 24.0);
+    c.j_s_nu13 = (C)(d.s_nu / 4.0);
+    c.j_h_nu13 = (C)((1.0 - 0.5 * d.s_nu) / 4.0);
+    c.j_m_t = (C)(-d.s_t / 8.0);
     c.darcy = p.darcy_A > 0;
     c.darcy_A = (C)p.darcy_A;
     c.darcy_eps = (C)(p.darcy_eps > 0 ? p.darcy_eps : 1e-3);

@@ -32,6 +32,10 @@ struct Coef {
     // enthalpy-porosity solid drag D = darcy_A (1 - f_l)^2 / (f_l^3 + darcy_eps)
     int darcy;
     C darcy_A, darcy_eps;
+    // adjoint of the D3Q19 relaxation: j_s_k = s_k / |row k|^2, j_h_k = (1 - s_k/2) / |row
+    // k|^2, j_m_t = -s_t / 8
+    C j_s_e, j_h_e, j_s_eps, j_h_eps, j_s_q, j_h_q, j_s_nu9, j_h_nu9, j_s_pi10, j_h_pi10,
+        j_s_nu11, j_h_nu11, j_s_pi12, j_h_pi12, j_s_nu13, j_h_nu13, j_m_t;
 };
 
 struct Args {
@@ -96,6 +100,9 @@ inline dim3 node_block_dims(int nx) {
     const int bx = nx >= 128 ? 128 : (nx > 32 ? 64 : 32);
     return dim3(bx, 128 / bx, 1);
 }
+// The adjoint's dJ/dL partials: one slot per warp of every block of the per-node grid
+// (blocks of 128 threads), so the reverse sweep reduces within warps only.
+constexpr int ADJ_WARPS_PER_BLOCK = 4;
 inline int node_grid_blocks(int nx, int ny, int nz) {
     const dim3 b = node_block_dims(nx);
     return ((nx + b.x - 1) / b.x) * ((ny + b.y - 1) / b.y) * nz;

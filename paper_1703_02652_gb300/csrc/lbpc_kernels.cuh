@@ -1247,34 +1247,31 @@ LBPC_HD C collide_adjoint(const Coef<C>& k, C d, C rho, C jx, C jy, C jz, C* lf,
         const C yz_z = (L[15] + L[16]) - (L[17] + L[18]);
         const C yz_p = (L[15] - L[16]) - (L[17] - L[18]);
         const C sax = a1 + a3 + a5, sdg = sxy + sxz + syz;
-        const C mu1 = (C(-30) * L[0] - C(11) * sax + C(8) * sdg) * C(1.0 / 2394.0);
-        const C mu2 = (C(12) * L[0] - C(4) * sax + sdg) * C(1.0 / 252.0);
-        const C mu3 = (b1 + xy_x + xz_x) * C(0.1);
-        const C mu4 = (C(-4) * b1 + xy_x + xz_x) * C(1.0 / 40.0);
-        const C mu5 = (b3 + xy_y + yz_y) * C(0.1);
-        const C mu6 = (C(-4) * b3 + xy_y + yz_y) * C(1.0 / 40.0);
-        const C mu7 = (b5 + xz_z + yz_z) * C(0.1);
-        const C mu8 = (C(-4) * b5 + xz_z + yz_z) * C(1.0 / 40.0);
-        const C mu9 = (C(2) * a1 - a3 - a5 + sxy + sxz - C(2) * syz) * C(1.0 / 36.0);
-        const C mu10 = (C(-4) * a1 + C(2) * (a3 + a5) + sxy + sxz - C(2) * syz) * C(1.0 / 72.0);
-        const C mu11 = (a3 - a5 + sxy - sxz) * C(1.0 / 12.0);
-        const C mu12 = (C(2) * (a5 - a3) + sxy - sxz) * C(1.0 / 24.0);
-        const C mu13 = xy_p * C(0.25), mu14 = yz_p * C(0.25), mu15 = xz_p * C(0.25);
-        const C mu16 = (xy_x - xz_x) * C(0.125), mu17 = (yz_y - xy_y) * C(0.125);
-        const C mu18 = (xz_z - yz_z) * C(0.125);
+        // raw moments R_k = (M lambda*_f)_k; mu_k = R_k / |row k|^2 enters only through the
+        // host constants j_s_k = s_k / |row k|^2 and j_h_k = (1 - s_k/2) / |row k|^2
+        const C R1 = C(-30) * L[0] - C(11) * sax + C(8) * sdg;
+        const C R2 = C(12) * L[0] - C(4) * sax + sdg;
+        const C tx = xy_x + xz_x, ty = xy_y + yz_y, tz = xz_z + yz_z;
+        const C mu3 = (b1 + tx) * C(0.1), mu5 = (b3 + ty) * C(0.1), mu7 = (b5 + tz) * C(0.1);
+        const C R4 = tx - C(4) * b1, R6 = ty - C(4) * b3, R8 = tz - C(4) * b5;
+        const C a35 = a3 + a5, h9 = (sxy + sxz) - C(2) * syz;
+        const C R9 = C(2) * a1 - a35 + h9;
+        const C R10 = C(2) * a35 - C(4) * a1 + h9;
+        const C k11 = sxy - sxz, a53 = a5 - a3;
+        const C R11 = k11 - a53, R12 = C(2) * a53 + k11;
+        const C R16 = xy_x - xz_x, R17 = yz_y - xy_y, R18 = xz_z - yz_z;
         // adjoints of m^eq (rate s_k) and of FF (weight 1 - s_k/2)
-        const C q1 = k.s_e * mu1, q2 = k.s_eps * mu2, q4 = k.s_q * mu4, q6 = k.s_q * mu6,
-                q8 = k.s_q * mu8;
-        const C w9 = k.s_nu * mu9 - C(0.5) * k.s_pi * mu10;
-        const C w11 = k.s_nu * mu11 - C(0.5) * k.s_pi * mu12;
-        const C q13 = k.s_nu * mu13, q14 = k.s_nu * mu14, q15 = k.s_nu * mu15;
-        const C r1 = (C(1) - C(0.5) * k.s_e) * mu1, r2 = (C(1) - C(0.5) * k.s_eps) * mu2;
-        const C hq = C(1) - C(0.5) * k.s_q;
-        const C r4 = hq * mu4, r6 = hq * mu6, r8 = hq * mu8;
-        const C hn = C(1) - C(0.5) * k.s_nu, hpi = C(1) - C(0.5) * k.s_pi;
-        const C v9 = hn * mu9 - C(0.5) * hpi * mu10;
-        const C v11 = hn * mu11 - C(0.5) * hpi * mu12;
-        const C r13 = hn * mu13, r14 = hn * mu14, r15 = hn * mu15;
+        const C q1 = k.j_s_e * R1, q2 = k.j_s_eps * R2;
+        const C q4 = k.j_s_q * R4, q6 = k.j_s_q * R6, q8 = k.j_s_q * R8;
+        const C q9 = k.j_s_nu9 * R9, q10 = k.j_s_pi10 * R10;
+        const C q11 = k.j_s_nu11 * R11, q12 = k.j_s_pi12 * R12;
+        const C w9 = q9 - C(0.5) * q10, w11 = q11 - C(0.5) * q12;
+        const C q13 = k.j_s_nu13 * xy_p, q14 = k.j_s_nu13 * yz_p, q15 = k.j_s_nu13 * xz_p;
+        const C r1 = k.j_h_e * R1, r2 = k.j_h_eps * R2;
+        const C r4 = k.j_h_q * R4, r6 = k.j_h_q * R6, r8 = k.j_h_q * R8;
+        const C v9 = k.j_h_nu9 * R9 - C(0.5) * k.j_h_pi10 * R10;
+        const C v11 = k.j_h_nu11 * R11 - C(0.5) * k.j_h_pi12 * R12;
+        const C r13 = k.j_h_nu13 * xy_p, r14 = k.j_h_nu13 * yz_p, r15 = k.j_h_nu13 * xz_p;
         const C u2 = ux * ux + uy * uy + uz * uz;
         const C c23 = C(2) / C(3);
         const C lrho = q1 * (C(-11) + C(19) * u2) + q2 * (C(3) - C(5.5) * u2) -
@@ -1292,7 +1289,7 @@ LBPC_HD C collide_adjoint(const Coef<C>& k, C d, C rho, C jx, C jy, C jz, C* lf,
         const C lFx = cf * ux - c23 * r4 + C(4) * v9 * ux + r13 * uy + r15 * uz + mu3;
         const C lFy = cf * uy - c23 * r6 - C(2) * v9 * uy + C(2) * v11 * uy + r13 * ux + r14 * uz + mu5;
         const C lFz = cf * uz - c23 * r8 - C(2) * v9 * uz - C(2) * v11 * uz + r14 * uy + r15 * ux + mu7;
-        // u = f_l us, F = F_b z + damp us, us = j + F_b/2 z, F_b = g beta (T - T_ref)
+        // u = phi us, F = F_b z + damp us, us = j + F_b/2 z, F_b = g beta (T - T_ref)
         const C lusx = phi * lux + damp * lFx;
         const C lusy = phi * luy + damp * lFy;
         const C lusz = phi * luz + damp * lFz;
@@ -1300,19 +1297,19 @@ LBPC_HD C collide_adjoint(const Coef<C>& k, C d, C rho, C jx, C jy, C jz, C* lf,
                        C(2) * (lFx * usx + lFy * usy + lFz * usz));
         const C lFb = lFz + C(0.5) * lusz;
         lT += k.gbeta * lFb;
-        // lambda_f = lambda*_f + M^T lambda_m, lambda_m = (lrho, -s mu, lj, ...)
+        // lambda_f = lambda*_f + M^T lambda_m, lambda_m = (lrho, -s mu, lj, ...), with the
+        // sums shared within axis pairs and diagonal quadruples as in the forward
         const C d0 = lrho, d3 = lusx, d5 = lusy, d7 = lusz;
-        const C d1 = -k.s_e * mu1, d2 = -k.s_eps * mu2;
-        const C d4 = -k.s_q * mu4, d6 = -k.s_q * mu6, d8 = -k.s_q * mu8;
-        const C d9 = -k.s_nu * mu9, d10 = -k.s_pi * mu10, d11 = -k.s_nu * mu11, d12 = -k.s_pi * mu12;
-        const C d13 = -k.s_nu * mu13, d14 = -k.s_nu * mu14, d15 = -k.s_nu * mu15;
-        const C d16 = -k.s_t * mu16, d17 = -k.s_t * mu17, d18 = -k.s_t * mu18;
+        const C d1 = -q1, d2 = -q2, d4 = -q4, d6 = -q6, d8 = -q8;
+        const C d9 = -q9, d10 = -q10, d11 = -q11, d12 = -q12;
+        const C d13 = -q13, d14 = -q14, d15 = -q15;
+        const C d16 = k.j_m_t * R16, d17 = k.j_m_t * R17, d18 = k.j_m_t * R18;
         lf[0] += d0 - C(30) * d1 + C(12) * d2;
         const C eax = d0 - C(11) * d1 - C(4) * d2;
         const C ox = d3 - C(4) * d4, oy = d5 - C(4) * d6, oz = d7 - C(4) * d8;
         const C ex1 = eax + C(2) * d9 - C(4) * d10;
-        const C ey1 = eax - d9 + C(2) * d10 + d11 - C(2) * d12;
-        const C ez1 = eax - d9 + C(2) * d10 - d11 + C(2) * d12;
+        const C cyz = eax - d9 + C(2) * d10, w1112 = d11 - C(2) * d12;
+        const C ey1 = cyz + w1112, ez1 = cyz - w1112;
         lf[1] += ex1 + ox;
         lf[2] += ex1 - ox;
         lf[3] += ey1 + oy;
@@ -1321,21 +1318,33 @@ LBPC_HD C collide_adjoint(const Coef<C>& k, C d, C rho, C jx, C jy, C jz, C* lf,
         lf[6] += ez1 - oz;
         const C edg = d0 + C(8) * d1 + d2;
         const C X = d3 + d4, Y = d5 + d6, Z = d7 + d8;
-        const C exy = edg + d9 + d10 + d11 + d12;
-        lf[7] += exy + X + Y + d13 + d16 - d17;
-        lf[8] += exy - X + Y - d13 - d16 - d17;
-        lf[9] += exy + X - Y - d13 + d16 + d17;
-        lf[10] += exy - X - Y + d13 - d16 + d17;
-        const C exz = edg + d9 + d10 - d11 - d12;
-        lf[11] += exz + X + Z + d15 - d16 + d18;
-        lf[12] += exz - X + Z - d15 + d16 + d18;
-        lf[13] += exz + X - Z - d15 - d16 - d18;
-        lf[14] += exz - X - Z + d15 + d16 - d18;
+        const C a910 = edg + d9 + d10, b1112 = d11 + d12;
+        const C exy = a910 + b1112, exz = a910 - b1112;
         const C eyz = edg - C(2) * d9 - C(2) * d10;
-        lf[15] += eyz + Y + Z + d14 + d17 - d18;
-        lf[16] += eyz - Y + Z - d14 - d17 - d18;
-        lf[17] += eyz + Y - Z - d14 + d17 + d18;
-        lf[18] += eyz - Y - Z + d14 - d17 + d18;
+        {
+            const C u = X + d16, v = Y - d17, Pp = exy + d13, Qq = exy - d13;
+            const C s = u + v, w = v - u;
+            lf[7] += Pp + s;
+            lf[8] += Qq + w;
+            lf[9] += Qq - w;
+            lf[10] += Pp - s;
+        }
+        {
+            const C u = X - d16, v = Z + d18, Pp = exz + d15, Qq = exz - d15;
+            const C s = u + v, w = v - u;
+            lf[11] += Pp + s;
+            lf[12] += Qq + w;
+            lf[13] += Qq - w;
+            lf[14] += Pp - s;
+        }
+        {
+            const C u = Y + d17, v = Z - d18, Pp = eyz + d14, Qq = eyz - d14;
+            const C s = u + v, w = v - u;
+            lf[15] += Pp + s;
+            lf[16] += Qq + w;
+            lf[17] += Qq - w;
+            lf[18] += Pp - s;
+        }
     }
     le += lT * dTde + lfl * dfde;
     lg[0] = le;
@@ -1657,6 +1666,12 @@ __device__ __forceinline__ int block_linear() {
     return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
 }
 
+// Per-warp slot of the adjoint's dJ/dL partials (ADJ_WARPS_PER_BLOCK per block).
+static_assert(STEP_THREADS / 32 == ADJ_WARPS_PER_BLOCK, "one partial slot per warp");
+__device__ __forceinline__ int warp_slot() {
+    return block_linear() * ADJ_WARPS_PER_BLOCK + ((threadIdx.x + blockDim.x * threadIdx.y) >> 5);
+}
+
 template <int P, bool FLOW>
 __global__ void __launch_bounds__(STEP_THREADS)
 k_adj_seed(const __grid_constant__ Args a, const TG<P>* __restrict__ gs,
@@ -1667,13 +1682,10 @@ k_adj_seed(const __grid_constant__ Args a, const TG<P>* __restrict__ gs,
     const int z = blockIdx.z;
     double dL = 0.0, fl = 0.0;
     if (x < a.nx && y < a.ny) dL = (double)adj_seed_node<P, FLOW>(a, x, y, z, gs, hp, lam, fl);
-    const double sL = block_sum(dL);
-    __syncthreads();
+    const double wL = warp_sum(dL);
+    if (((threadIdx.x + blockDim.x * threadIdx.y) & 31) == 0) Lpart[warp_slot()] = wL;
     const double sJ = block_sum(fl);
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-        Lpart[block_linear()] = sL;
-        Jpart[block_linear()] = sJ;
-    }
+    if (threadIdx.x == 0 && threadIdx.y == 0) Jpart[block_linear()] = sJ;
 }
 
 template <int P, bool FLOW>
@@ -1694,8 +1706,9 @@ k_adj_reverse(const __grid_constant__ Args a, const CT<P>* __restrict__ lin,
             dL = (double)adj_reverse_node<P, FLOW>(a, make_nb(a, x, y, z), x, y, z, lin, lout,
                                                    tape_e, tape_m, wface, gtw);
     }
-    const double s = block_sum(dL);
-    if (threadIdx.x == 0 && threadIdx.y == 0) Lpart[block_linear()] += s;
+    // warp partials only: no block barrier in the reverse sweep
+    const double w = warp_sum(dL);
+    if (((threadIdx.x + blockDim.x * threadIdx.y) & 31) == 0) Lpart[warp_slot()] += w;
 }
 
 // Reverse step, two nodes per thread along x (even nx); the pull kernels' vote.
@@ -1721,8 +1734,9 @@ k_adj_reverse_x2(const __grid_constant__ Args a, const CT<P>* __restrict__ lin,
                                                         tape_e, tape_m, wface, gtw);
         }
     }
-    const double s = block_sum(dL);
-    if (threadIdx.x == 0 && threadIdx.y == 0) Lpart[block_linear()] += s;
+    // warp partials only: no block barrier in the reverse sweep
+    const double w = warp_sum(dL);
+    if (((threadIdx.x + blockDim.x * threadIdx.y) & 31) == 0) Lpart[warp_slot()] += w;
 }
 
 // ---------------------------------------------------------------------------------
