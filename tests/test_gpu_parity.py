@@ -215,6 +215,65 @@ def test_one_step_from_random_state(precision, streaming, flow_model, nx):
         o.set_distributions(f1.cpu().numpy() if f1 is not None else None, g1.cpu().numpy())
 
 
+# Rows of 256 nodes: one 128-thread block of node pairs per row, the two x faces in
+# different warps of the block; x walls (isothermal: anti-bounce-back of g, bounce-back of
+# f, a per-node wall field) and x periodic (the wrap crosses warps), every storage mode,
+# both solid closures.
+@pytest.mark.parametrize("precision", [inp.FP32, inp.FP16, inp.BF16, inp.FP16_G32, inp.BF16_G32])
+@pytest.mark.parametrize("flow_model,darcy_A", [(inp.FLOW_MRT, 0.0), (inp.FLOW_SRT, 0.0),
+                                                (inp.FLOW_NONE, 0.0), (inp.FLOW_MRT, 3.0)])
+@pytest.mark.parametrize("xbc", [inp.ISOTHERMAL, inp.PERIODIC])
+def test_one_step_from_random_state_wide_rows(precision, flow_model, darcy_A, xbc):
+    shape = (256, 6, 5)
+    bc = [xbc, xbc, inp.PERIODIC, inp.PERIODIC, inp.ADIABATIC, inp.ADIABATIC]
+    p = inp.Params(flow_model=flow_model, precision=precision, streaming=inp.PULL, Ra=5e4,
+                   Pr=0.5, St=0.7, tau_g=0.0 if flow_model else 0.9, bc=bc, darcy_A=darcy_A)
+    f, gq = inp.random_state(shape, seed=6, flow=flow_model != 0)
+    dev = torch.device("cuda")
+    g = LBPC(shape, p)
+    if xbc == inp.ISOTHERMAL:
+        g.set_wall_temperature(0, inp.wall_temperature_field(6, 5, seed=2))
+    g.set_distributions(torch.from_numpy(f).to(dev) if f is not None else None,
+                        torch.from_numpy(gq).to(dev))
+    f0, g0 = g.distributions()
+    o = oracle.Oracle(shape, p)
+    if xbc == inp.ISOTHERMAL:
+        o.set_wall_temperature(0, inp.wall_temperature_field(6, 5, seed=2))
+    o.set_distributions(f0.cpu().numpy() if f0 is not None else None, g0.cpu().numpy())
+    for _ in range(3):
+        g.step(1)
+        o.step(1)
+        f1, g1 = g.distributions()
+        fo, go = o.distributions()
+        g1n = g1.cpu().numpy()
+        assert np.abs(g1n[1:] - go[1:]).max() <= TOL[precision]
+        assert np.abs(g1n[0] - go[0]).max() <= 6 * TOL[precision]
+        if flow_model:
+            assert np.abs(f1.cpu().numpy() - fo).max() <= TOL[precision]
+        o.set_distributions(f1.cpu().numpy() if f1 is not None else None, g1.cpu().numpy())
+
+
+@pytest.mark.parametrize("precision,tol", [(inp.FP32, 1e-5), (inp.FP16, 1e-3)])
+@pytest.mark.parametrize("shape", [(256, 8, 6), (512, 4, 3)])
+def test_wide_row_cavity_tracks_oracle(precision, tol, shape):
+    """Rows of one and of two 128-pair blocks, 300 steps of the melting cavity against the
+    oracle, and the diagnostics' sum of h against the fields."""
+    p = inp.Params(precision=precision, Ra=1e5, Pr=0.71, St=1.0)
+    h0 = np.random.default_rng(7).uniform(-1e-6, 1e-6, int(np.prod(shape)))
+    g, o = _pair(shape, p, h0=h0)
+    g.step(300)
+    o.step(300)
+    F = _np(g.fields())
+    err = _maxerr(F, o.fields(), ("T", "fl", "rho", "h"))
+    assert max(err.values()) <= tol, err
+    # the diagnostics reduce the GPU's own h field in FP64; against the oracle the sum can
+    # differ by at most the per-node tolerance times the node count (isothermal walls let
+    # FP32-rounded fluxes in and out every step)
+    sg, so = g.scalars(), o.diagnostics()
+    assert abs(sg["sum_h"] - F["h"].sum()) <= 1e-12 * abs(F["h"]).sum()
+    assert abs(sg["sum_h"] - so["sum_h"]) <= tol * F["h"].size
+
+
 @pytest.mark.parametrize("precision,tol", [(inp.FP64, 1e-13), (inp.FP32, 2e-6), (inp.FP16, 1e-3)])
 def test_aa_and_pull_agree(precision, tol):
     """The two streaming schemes compute the same arithmetic on the same values; they
