@@ -218,7 +218,9 @@ lbpc_status lbpc_load(lbpc_handle *h, const void *host_buf, size_t bytes);
  * every ckpt_every-step segment but the last and writes the per-step macroscopic tape
  * (h - h_s, rho and j in the compute precision: 20 B per node and step in FP32)
  * over the last segment; the backward sweeps that tape backwards, then for each earlier
- * segment recomputes it from its checkpoint writing the tape, and sweeps it backwards.  The adjoint populations are kept in the compute precision;
+ * segment recomputes it from its checkpoint writing the tape (in the checkpoint slots: the
+ * handle's own state is not touched), and sweeps it backwards.  The adjoint populations
+ * are kept in the compute precision;
  * the parameter gradients accumulate in FP64.  Pull streaming only (LBPC_ERR_STATE
  * otherwise).  dev_ws: device, 256-byte aligned, >= lbpc_adjoint_workspace_bytes().
  *

@@ -642,7 +642,8 @@ AdjLayout adj_layout(const lbpc_handle* h, int nsteps, int k) {
     L.off_hp = L.off_g + align_up(6 * N * Sg);
     L.ckpt_bytes = L.off_hp + align_up(8 * N);
     size_t off = 0;
-    L.ckpt = off; off += (size_t)(L.nseg + 1) * L.ckpt_bytes;
+    // slots 0 .. nseg - 2: segment starts; slot nseg - 1: spare for the recompute
+    L.ckpt = off; off += (size_t)(L.nseg > 1 ? L.nseg : 0) * L.ckpt_bytes;
     L.tape_e = off; off = align_up(off + (size_t)k * N * Cb);
     L.tape_m = off; off = align_up(off + (flow ? (size_t)k * 4 * N * Cb : 0));
     const size_t lam = (size_t)(flow ? 26 : 7) * N * Cb;
@@ -666,17 +667,6 @@ lbpc_status save_state(lbpc_handle* h, char* dst) {
         LBPC_CK(h, cudaMemcpyAsync(dst + A.off_f, h->f[h->cur], 19 * N * Sf, cudaMemcpyDeviceToDevice, h->stream));
     LBPC_CK(h, cudaMemcpyAsync(dst + A.off_g, h->g[h->cur], 6 * N * Sg, cudaMemcpyDeviceToDevice, h->stream));
     LBPC_CK(h, cudaMemcpyAsync(dst + A.off_hp, h->hp, 8 * N, cudaMemcpyDeviceToDevice, h->stream));
-    return LBPC_OK;
-}
-
-lbpc_status restore_state(lbpc_handle* h, const char* src) {
-    auto& A = h->adj;
-    const size_t N = (size_t)h->N, Sf = h->L->f_bytes, Sg = h->L->g_bytes;
-    h->cur = 0;
-    if (h->p.flow_model != LBPC_FLOW_NONE)
-        LBPC_CK(h, cudaMemcpyAsync(h->f[0], src + A.off_f, 19 * N * Sf, cudaMemcpyDeviceToDevice, h->stream));
-    LBPC_CK(h, cudaMemcpyAsync(h->g[0], src + A.off_g, 6 * N * Sg, cudaMemcpyDeviceToDevice, h->stream));
-    LBPC_CK(h, cudaMemcpyAsync(h->hp, src + A.off_hp, 8 * N, cudaMemcpyDeviceToDevice, h->stream));
     return LBPC_OK;
 }
 
@@ -724,31 +714,45 @@ lbpc_status lbpc_adjoint_forward(lbpc_handle* h, int nsteps, int ckpt_every, voi
     // Forward with a checkpoint at the start of every segment but the last, and one of the
     // final state.  The last segment writes its tape as it goes, so the backward sweep
     // starts on it without recomputing it (and needs no checkpoint at its start).
+    // A step that ends on a later segment start writes its populations straight into that
+    // checkpoint (only h', updated in place, is copied), and the next step reads them from
+    // there: the populations of those checkpoints cost no extra copy.
     const int tail = (L.nseg - 1) * ckpt_every;
     if (L.nseg > 1) {
         s = save_state(h, A.ckpt);
         if (s != LBPC_OK) return s;
     }
+    const bool flow = h->p.flow_model != LBPC_FLOW_NONE;
+    const void* sf = h->f[h->cur];  // where the current populations are
+    const void* sg = h->g[h->cur];
     for (int i = 0; i < nsteps; i++) {
+        const int nb = 1 - h->cur;  // the lattice buffer the step writes unless redirected
         if (i < tail) {
-            h->L->step(h->args, STEP_PULL, h->f[h->cur], h->f[1 - h->cur], h->g[h->cur],
-                       h->g[1 - h->cur], h->hp, h->stream);
+            const bool to_ckpt = (i + 1) % ckpt_every == 0 && i + 1 < tail;
+            char* slot = A.ckpt + (size_t)((i + 1) / ckpt_every) * A.ckpt_bytes;
+            void* df = to_ckpt ? (flow ? slot + A.off_f : nullptr) : h->f[nb];
+            void* dg = to_ckpt ? slot + A.off_g : h->g[nb];
+            h->L->step(h->args, STEP_PULL, sf, df, sg, dg, h->hp, h->stream);
+            sf = df;
+            sg = dg;
+            if (to_ckpt) {
+                LBPC_CK(h, cudaMemcpyAsync(slot + A.off_hp, h->hp, 8 * (size_t)h->N,
+                                           cudaMemcpyDeviceToDevice, h->stream));
+            } else {
+                h->cur = nb;
+            }
         } else {
             const size_t t = (size_t)(i - tail);
-            h->L->step_tape(h->args, h->f[h->cur], h->f[1 - h->cur], h->g[h->cur], h->g[1 - h->cur],
-                            h->hp, (char*)A.tape_e + t * h->N * h->L->compute_bytes,
+            h->L->step_tape(h->args, sf, h->f[nb], sg, h->g[nb], h->hp,
+                            (char*)A.tape_e + t * h->N * h->L->compute_bytes,
                             (char*)A.tape_m + t * 4 * h->N * h->L->compute_bytes, h->stream);
+            sf = h->f[nb];
+            sg = h->g[nb];
+            h->cur = nb;
         }
-        h->cur = 1 - h->cur;
         h->step++;
         h->launches++;
-        if ((i + 1) % ckpt_every == 0 && i + 1 < tail) {
-            s = save_state(h, A.ckpt + (size_t)((i + 1) / ckpt_every) * A.ckpt_bytes);
-            if (s != LBPC_OK) return s;
-        }
     }
-    s = save_state(h, A.ckpt + (size_t)A.nseg * A.ckpt_bytes);
-    if (s != LBPC_OK) return s;
     // seed lambda_N = d f_l / dh (and J = sum f_l, the direct dJ/dL part)
     h->L->adj_seed(h->args, h->g[h->cur], h->hp, A.lam[0], A.Lpart, A.Jpart, h->stream);
     k_sum<<<1, 256, 0, h->stream>>>(A.Jpart, A.nblocks, A.red);
@@ -777,13 +781,21 @@ lbpc_status lbpc_adjoint_backward(lbpc_handle* h, int face, double* dJ_dTw_host,
     for (int seg = A.nseg - 1; seg >= 0; seg--) {
         const int start = seg * A.k, len = std::min(A.k, A.nsteps - start);
         if (seg < A.nseg - 1) {  // the last segment's tape is the forward's
-            s = restore_state(h, A.ckpt + (size_t)seg * A.ckpt_bytes);
-            if (s != LBPC_OK) return s;
-            for (int t = 0; t < len; t++) {  // recompute the segment, writing the tape
-                h->L->step_tape(h->args, h->f[h->cur], h->f[1 - h->cur], h->g[h->cur],
-                                h->g[1 - h->cur], h->hp, (char*)A.tape_e + (size_t)t * N * Cb,
+            // recompute the segment, writing the tape, in checkpoint slots seg and seg + 1
+            // (both free from here on: slot seg + 1 belongs to a segment already swept, or is
+            // the spare slot), with slot seg's h' updated in place: the handle's own lattice
+            // keeps the final state throughout
+            char* ck[2] = {A.ckpt + (size_t)seg * A.ckpt_bytes,
+                           A.ckpt + (size_t)(seg + 1) * A.ckpt_bytes};
+            const bool flow = h->p.flow_model != LBPC_FLOW_NONE;
+            double* hp = (double*)(ck[0] + A.off_hp);
+            for (int t = 0; t < len; t++) {
+                char* src = ck[t & 1];
+                char* dst = ck[(t + 1) & 1];
+                h->L->step_tape(h->args, flow ? src + A.off_f : nullptr,
+                                flow ? dst + A.off_f : nullptr, src + A.off_g, dst + A.off_g, hp,
+                                (char*)A.tape_e + (size_t)t * N * Cb,
                                 (char*)A.tape_m + (size_t)t * 4 * N * Cb, h->stream);
-                h->cur = 1 - h->cur;
             }
             h->launches += len;
         }
@@ -797,8 +809,6 @@ lbpc_status lbpc_adjoint_backward(lbpc_handle* h, int face, double* dJ_dTw_host,
     k_sum<<<1, 256, 0, h->stream>>>(A.Lpart, A.nblocks * ADJ_WARPS_PER_BLOCK, A.red + 1);
     h->launches++;
     LBPC_CK(h, cudaGetLastError());
-    s = restore_state(h, A.ckpt + (size_t)A.nseg * A.ckpt_bytes);  // back to the final state
-    if (s != LBPC_OK) return s;
     double dJdL = 0.0;
     LBPC_CK(h, cudaMemcpyAsync(&dJdL, A.red + 1, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     if (dJ_dTw_host)
