@@ -237,10 +237,33 @@ LBPC_HD C abb_source(const Args& a, const Coef<C>& k, int face, int x, int y, in
 // ---------------------------------------------------------------------------------
 // Gathers: pre-collision populations of node n for each memory layout.
 // ---------------------------------------------------------------------------------
+// 16-bit populations (and pairs of them): read-only loads that ask L2 to fetch 256 bytes
+// around each miss; other types: plain read-only loads.
+template <class X> struct Is16 { static constexpr bool value = false; };
+template <> struct Is16<__half> { static constexpr bool value = true; };
+template <> struct Is16<__nv_bfloat16> { static constexpr bool value = true; };
+template <> struct Is16<__half2> { static constexpr bool value = true; };
+template <> struct Is16<__nv_bfloat162> { static constexpr bool value = true; };
+#if defined(__CUDA_ARCH__)
+template <class X>
+__device__ __forceinline__ X ld_nc(const X* p) {
+    if constexpr (Is16<X>::value && sizeof(X) == 2) {
+        unsigned short v;
+        asm("ld.global.nc.L2::256B.u16 %0, [%1];" : "=h"(v) : "l"(p));
+        return *reinterpret_cast<X*>(&v);
+    } else if constexpr (Is16<X>::value && sizeof(X) == 4) {
+        unsigned v;
+        asm("ld.global.nc.L2::256B.u32 %0, [%1];" : "=r"(v) : "l"(p));
+        return *reinterpret_cast<X*>(&v);
+    } else {
+        return __ldg(p);
+    }
+}
+#endif
 template <int P, int LAYOUT, bool NC>
 LBPC_HD typename Store<P>::T ldv(const typename Store<P>::T* p) {
 #if defined(__CUDA_ARCH__)
-    if constexpr (NC) return __ldg(p);
+    if constexpr (NC) return ld_nc(p);
 #endif
     return *p;
 }
@@ -249,7 +272,7 @@ LBPC_HD typename Store<P>::T ldv(const typename Store<P>::T* p) {
 template <bool NC, class X>
 LBPC_HD X ld_any(const X* p) {
 #if defined(__CUDA_ARCH__)
-    if constexpr (NC) return __ldg(p);
+    if constexpr (NC) return ld_nc(p);
 #endif
     return *p;
 }
