@@ -7,7 +7,8 @@ time step of every lattice node.  The working set (3.6 GB) is far larger than th
 129 MB L2, so no flush is needed between steps.
 
 Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle instead (on a
-256x32x32 slab of the same cavity, host cores), the reference arm of this build.
+256x32x32 slab of the same cavity, host cores): the paper ships no code, so the oracle is
+the reference.
 Under torchrun every rank runs its own replica (the lattice is not sharded).
 """
 from __future__ import annotations
