@@ -274,3 +274,65 @@ def test_solid_closures_reach_the_steady_drag_velocity(darcy_A, fl0):
     assert np.abs(F["u"][2] - uz).max() <= 1e-12 * abs(uz)
     assert np.abs(F["u"][:2]).max() <= 1e-15
     assert np.abs(F["fl"] - fl0).max() == 0.0
+
+
+_SAMPLED_CASES = [
+    # (shape, bc of the six faces, flow model, enthalpy model, enthalpy-porosity A)
+    ((1, 1, 1), [inp.PERIODIC] * 6, inp.FLOW_MRT, inp.ENTH_MRT, 0.0),
+    ((1, 1, 1), [inp.ISOTHERMAL, inp.ADIABATIC, inp.ADIABATIC, inp.ISOTHERMAL,
+                 inp.ISOTHERMAL, inp.ADIABATIC], inp.FLOW_MRT, inp.ENTH_MRT, 0.0),
+    ((3, 2, 5), [inp.ISOTHERMAL, inp.ISOTHERMAL, inp.ADIABATIC, inp.ADIABATIC,
+                 inp.ADIABATIC, inp.ADIABATIC], inp.FLOW_MRT, inp.ENTH_MRT, 0.0),
+    ((3, 2, 5), [inp.ISOTHERMAL, inp.ADIABATIC, inp.PERIODIC, inp.PERIODIC,
+                 inp.ADIABATIC, inp.ISOTHERMAL], inp.FLOW_SRT, inp.ENTH_SRT, 0.0),
+    ((6, 5, 4), [inp.PERIODIC, inp.PERIODIC, inp.ISOTHERMAL, inp.ADIABATIC,
+                 inp.ISOTHERMAL, inp.ISOTHERMAL], inp.FLOW_MRT, inp.ENTH_SRT, 0.0),
+    ((6, 5, 4), [inp.ADIABATIC, inp.ISOTHERMAL, inp.ISOTHERMAL, inp.ISOTHERMAL,
+                 inp.PERIODIC, inp.PERIODIC], inp.FLOW_SRT, inp.ENTH_MRT, 0.0),
+    ((5, 4, 3), [inp.ISOTHERMAL, inp.ISOTHERMAL, inp.ADIABATIC, inp.ADIABATIC,
+                 inp.ADIABATIC, inp.ADIABATIC], inp.FLOW_MRT, inp.ENTH_MRT, 5.0),
+    ((4, 3, 7), [inp.ISOTHERMAL, inp.ADIABATIC, inp.ISOTHERMAL, inp.ADIABATIC,
+                 inp.PERIODIC, inp.PERIODIC], inp.FLOW_NONE, inp.ENTH_MRT, 0.0),
+    ((7, 1, 2), [inp.ISOTHERMAL, inp.ISOTHERMAL, inp.PERIODIC, inp.PERIODIC,
+                 inp.PERIODIC, inp.PERIODIC], inp.FLOW_NONE, inp.ENTH_SRT, 0.0),
+]
+
+
+@pytest.mark.parametrize("case", range(len(_SAMPLED_CASES)))
+def test_sampled_update_equals_the_full_step(case):
+    """The node-by-node update (used to check single nodes of lattices too large for a
+    full oracle step) must give the post-stream populations of one full step exactly.
+    It rebuilds the pull stream of Eq. 5 / Eq. 50 and the half-way wall rules
+    (bounce-back of f and of g on adiabatic faces, anti-bounce-back -g*_abar +
+    omega_T C_p,ref T_w on isothermal faces) on its own, one node at a time, so a wrong
+    face, upwind index or opposite slot there differs from the full step at some node.
+    Every lattice here reaches each rule it has: periodic wraps, all six face kinds, edges
+    and corners, per-node wall temperatures, extents of one node."""
+    shape, bc, flow_model, enth_model, darcy_A = _SAMPLED_CASES[case]
+    rng = np.random.default_rng(40 + case)
+    T_wall = list(rng.uniform(-0.5, 1.5, 6))
+    p = inp.Params(flow_model=flow_model, enth_model=enth_model, precision=inp.FP64, bc=bc,
+                   T_wall=T_wall, Ra=1e5, Pr=0.7, St=1.0, darcy_A=darcy_A,
+                   tau_g=0.8 if flow_model == inp.FLOW_NONE else 0.0)
+    o = oracle.Oracle(shape, p)
+    nx, ny, nz = shape
+    area = [ny * nz, ny * nz, nx * nz, nx * nz, nx * ny, nx * ny]
+    for face in range(6):
+        if bc[face] == inp.ISOTHERMAL and face % 2 == case % 2:
+            o.set_wall_temperature(face, rng.uniform(-0.5, 1.5, area[face]))
+    f, g = inp.random_state(shape, seed=case, flow=o.flow)
+    o.set_distributions(f, g)
+    f0, g0 = o.distributions()
+    everywhere = np.arange(o.N)
+    fo, go = o.update_sampled(f0, g0, everywhere)
+    some = rng.integers(0, o.N, size=2 * o.N + 3)  # random order, with repeats
+    fs, gs = o.update_sampled(f0, g0, some)
+    o.step(1)
+    f1, g1 = o.distributions()
+    assert np.array_equal(go, g1.T)
+    assert np.array_equal(gs, g1.T[some])
+    if o.flow:
+        assert np.array_equal(fo, f1.T)
+        assert np.array_equal(fs, f1.T[some])
+    # the step changed the state, so equality is not a copy of the input
+    assert np.abs(g1 - g0).max() > 1e-3
