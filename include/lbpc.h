@@ -48,10 +48,13 @@ enum { LBPC_PERIODIC = 0, LBPC_ISOTHERMAL = 1, LBPC_ADIABATIC = 2 };
 enum { LBPC_FLOW_NONE = 0, LBPC_FLOW_MRT = 1, LBPC_FLOW_SRT = 2 };
 enum { LBPC_ENTH_MRT = 1, LBPC_ENTH_SRT = 2 };
 /* storage precision of the populations; collision runs in FP64 for LBPC_FP64 and in
- * FP32 registers otherwise; h', the H -> (T, f_l) inversion and reductions are FP64.
- * FP16S / BF16S store f - w_a and g_a - (omega_T/2) Cp_ref Tref in 16 bits (116 B per
- * node update); the _G32 modes store f that way and g in FP32 (140 B), which keeps the
- * enthalpy populations and the wall fluxes they carry at FP32 resolution. */
+ * FP32 registers otherwise.  h' and the reductions are FP64 in every mode.  The H -> (T,
+ * f_l) inversion of Eq. 2 decides its branch on the FP64 excess h - h_s, exactly, in every
+ * mode, and reports FP64 fields; the FP32 collision takes T and f_l formed in FP32 from
+ * h - h_s rounded once to nearest.  FP16S / BF16S store f - w_a and g_a - (omega_T/2)
+ * Cp_ref Tref in 16 bits (116 B per node update), the g populations crossing isothermal
+ * faces kept to FP32 by a residual per boundary node; the _G32 modes store f that way and
+ * g in FP32 (140 B), which keeps every enthalpy population at FP32 resolution. */
 enum { LBPC_FP64 = 0, LBPC_FP32 = 1, LBPC_FP16S = 2, LBPC_BF16S = 3, LBPC_FP16S_G32 = 4,
        LBPC_BF16S_G32 = 5 };
 enum { LBPC_PULL = 0, LBPC_AA = 1 };
@@ -77,7 +80,8 @@ enum { LBPC_PULL = 0, LBPC_AA = 1 };
  *  sigma4 > 0  sets sigma_4 = sigma_5 = sigma_6; <= 0 uses 2 - sigma_chi (Eq. 47).
  *  h0          uniform initial enthalpy (lbpc_set_initial_h overrides per node).
  *  report_every > 0  record diagnostics every so many steps (lbpc_get_history) and check
- *              for divergence at the end of lbpc_step; 0 disables both.
+ *              for divergence at the diagnostics points; 0: no history, and every
+ *              lbpc_step call checks g and h' for non-finite values once, at its end.
  *  lambda_s, lambda_l  both > 0: per-phase thermal conductivities (Eq. 1, rho0 = 1; Sec.
  *              3.1.2 case (b)), conduction only (flow_model NONE, no tau_g).  The
  *              enthalpy rates then follow per node from f_l: chi = lambda(f_l) / C_p,ref
@@ -133,18 +137,25 @@ enum { LBPC_L_CHI = 0, LBPC_L_NU, LBPC_L_GBETA, LBPC_L_SIGMA_CHI, LBPC_L_SIGMA4,
        LBPC_L_LATENT, LBPC_L_HS, LBPC_L_HL, LBPC_L_TAU_G, LBPC_L_TAU_F, LBPC_L_S_E,
        LBPC_L_S_EPS, LBPC_L_S_Q, LBPC_L_S_PI, LBPC_L_S_T, LBPC_L_U0, LBPC_L_COUNT };
 
-/* sizeof(lbpc_params) as compiled into the library (binding layout check). */
+/* sizeof(lbpc_params) as compiled into the library, and the ABI version (binding layout
+ * checks).  Passage: none (interface only; the paper has no software interface). */
 size_t lbpc_params_size(void);
 int lbpc_abi_version(void);
 
 /* Bytes of device workspace lbpc_create needs for this lattice and parameter block
  * (0 if the parameters are invalid).  Per node: 2 x (19 + 6) populations (pull) or
- * 1 x (19 + 6) (AA) in the storage precision, 8 B of h', 8 B of field staging. */
+ * 1 x (19 + 6) (AA) in the storage precision, 8 B of h', 8 B of field staging; per face
+ * node: 8 B of wall temperature, and 4 B of wall residual with 16-bit g.
+ * Passage: the state of the two lattices, D3Q19 (Eq. 48) and D3Q7 (Eq. 3); the sizing
+ * itself has no counterpart in the paper.  No CUDA call. */
 size_t lbpc_workspace_bytes(int nx, int ny, int nz, const lbpc_params *p);
 
 /* Validate p, map it to lattice units, carve the state out of dev_ws (device, 256-byte
  * aligned, >= lbpc_workspace_bytes) and initialise the equilibrium state at uniform
- * h0 and uniform wall temperatures.  cuda_stream is a cudaStream_t (NULL: legacy
+ * h0 and uniform wall temperatures.  Passages: the mapping of Eq. 20 / 34 (diffusivity
+ * and sigma_chi), Eq. 59 (viscosity and s_nu), Eq. 64 (Ra, Pr, St), Eq. 2 (h_s, L) and
+ * Eq. 47 (sigma_4..6); the initial state f^eq (Eq. 53 at rho = 1, u = 0) and g^eq of
+ * Eq. 7; the cavity set-up of Sec. 3.3.  cuda_stream is a cudaStream_t (NULL: legacy
  * default stream) used for every later launch.  On success *out owns no memory but
  * the handle itself; dev_ws must outlive it.  Sizes: nx ny nz < 2^31 nodes, ny and nz
  * <= 65535 (grid limits).  Errors: LBPC_ERR_PARAM (before any CUDA call),
@@ -153,61 +164,86 @@ lbpc_status lbpc_create(int nx, int ny, int nz, const lbpc_params *p, void *dev_
                         size_t ws_bytes, void *cuda_stream, lbpc_handle **out);
 
 /* Host-only: the derived lattice constants lbpc_create would use (out: n >= LBPC_L_COUNT
- * doubles).  No CUDA call; LBPC_ERR_PARAM for an invalid parameter block. */
+ * doubles).  No CUDA call; LBPC_ERR_PARAM for an invalid parameter block.  Passages: Eq.
+ * 20, 34, 47, 52, 59, 64 and Eq. 2 (the constants listed in LBPC_L_*). */
 lbpc_status lbpc_lattice_constants(int nx, int ny, int nz, const lbpc_params *p, double *out,
                                    int n);
 
 /* Reset to t = 0: f = f^eq(rho = 1, u = 0), g = g^eq(h, T(h), 0) (Eq. 7) from h
- * (host, N values; NULL = uniform p->h0). */
+ * (host, N values; NULL = uniform p->h0).  Passages: Eq. 7 and Eq. 2 (T(h)); the initial
+ * conditions of Sec. 3.1-3.3 (a uniform or perturbed enthalpy field).  Synchronous;
+ * LBPC_ERR_CUDA if a copy or launch fails. */
 lbpc_status lbpc_set_initial_h(lbpc_handle *h, const double *h_host);
 
 /* Per-node temperature of an ISOTHERMAL face (host, face-area values: y + ny z for
  * -x/+x, x + nx z for -y/+y, x + nx y for -z/+z).  Takes effect from the next step;
- * the current populations are kept. */
+ * the current populations are kept.  Passage: the isothermal walls of Sec. 3.1-3.3
+ * (T_h, T_1 held at a face); the per-node field is the adjoint's control and has no
+ * counterpart in the paper.  LBPC_ERR_PARAM for a bad face or a NULL field. */
 lbpc_status lbpc_set_wall_temperature(lbpc_handle *h, int face, const double *T_host);
 
-/* Advance n >= 0 time steps on the handle's stream (asynchronous unless report_every
- * > 0 and the call passes a diagnostics point, in which case the call waits for the stream
- * and returns LBPC_ERR_DIVERGED if the last diagnostics it recorded saw a non-finite
- * value).  LBPC_ERR_STATE after divergence. */
+/* Advance n >= 0 time steps on the handle's stream.  Passages: one step is the pull
+ * form of Eq. 5 (enthalpy, collision Eq. 6 SRT or Eq. 21-25 MRT with Eq. 47) and of Eq.
+ * 50 (flow, collision Eq. 49 with Eq. 51-54), coupled through Eq. 2, Eq. 55 and Eq. 56,
+ * with the walls of Sec. 3.1-3.3.  Divergence checks: with report_every > 0 the call is
+ * asynchronous unless it passes a diagnostics point; then it waits for the stream and
+ * returns LBPC_ERR_DIVERGED if the last diagnostics it recorded saw a non-finite h or rho.
+ * With report_every = 0 every call with n > 0 ends with one read of the stored g
+ * populations and the FP64 rest channel h' (6 g values + 8 B per node; a non-finite f
+ * reaches g within one step), waits for the stream and returns LBPC_ERR_DIVERGED if a
+ * value there is not finite.  LBPC_ERR_STATE
+ * after divergence, until lbpc_set_initial_h, lbpc_set_distributions_dev or lbpc_load. */
 lbpc_status lbpc_step(lbpc_handle *h, int n);
 
-/* Macroscopic fields of the current state (after the last stream, Eq. 2 / Eq. 56),
- * FP64, N values each (u: 3N).  Any pointer may be NULL; mask selects LBPC_FIELD_*.
- * _dev: device pointers, stream-ordered.  Host variant: synchronous. */
+/* Macroscopic fields of the current state (after the last stream), FP64, N values each
+ * (u: 3N).  Passages: h = sum_a g_a (Eq. 9), T and f_l by the FP64 inversion of Eq. 2,
+ * rho and u of Eq. 56 with the buoyancy of Eq. 55 and the solid closure.  Any pointer may
+ * be NULL; mask selects LBPC_FIELD_*.  _dev: device pointers, stream-ordered.  Host
+ * variant: synchronous (stages through the workspace).  LBPC_ERR_CUDA on a failed copy. */
 lbpc_status lbpc_get_fields(lbpc_handle *h, unsigned mask, double *T, double *fl, double *hh,
                             double *rho, double *u);
 lbpc_status lbpc_get_fields_dev(lbpc_handle *h, double *T, double *fl, double *hh, double *rho,
                                 double *u);
 
-/* Scalar diagnostics of the current state (host, n >= LBPC_S_COUNT doubles). Synchronous. */
+/* Scalar diagnostics of the current state (host, n >= LBPC_S_COUNT doubles), FP64
+ * reductions in a fixed order.  Passages: the Nusselt number of Eq. 65 (3D form, see
+ * LBPC_S_NU_HOT), the liquid fraction and melt-front position reported in Sec. 3.2.2 and
+ * Sec. 3.3; total enthalpy and mass are the conserved sums of Eq. 9 and Eq. 56 (rho).
+ * Synchronous.  LBPC_ERR_PARAM if n < LBPC_S_COUNT. */
 lbpc_status lbpc_get_scalars(lbpc_handle *h, double *out, int n);
 
 /* Rows recorded every report_every steps since the last reset (host, max_rows x
  * LBPC_S_COUNT doubles, row-major); *rows receives the number of rows written.  The
- * device keeps the most recent LBPC_HISTORY_ROWS rows. */
+ * device keeps the most recent LBPC_HISTORY_ROWS rows.  Passage: the time histories of
+ * liquid fraction and Nusselt number of Sec. 3.2.2 / 3.3 (scalars as lbpc_get_scalars).
+ * Synchronous. */
 #define LBPC_HISTORY_ROWS 4096
 lbpc_status lbpc_get_history(lbpc_handle *h, double *out, int max_rows, int *rows);
 
 /* Pre-collision populations of the current state in FP64 (device): f (19 x N, absent
  * when flow_model = NONE: may be NULL) and g (7 x N, g_0 = h').  _set_ loads such a
- * state (t unchanged); the state is then rounded to the storage precision. */
+ * state (t unchanged); the state is then rounded to the storage precision.  Passage: the
+ * populations f_a of Eq. 48-50 and g_a of Eq. 3-5 (D3Q19 / D3Q7 velocity order of the
+ * paper).  Stream-ordered; _set_ clears a divergence. */
 lbpc_status lbpc_get_distributions_dev(lbpc_handle *h, double *f, double *g);
 lbpc_status lbpc_set_distributions_dev(lbpc_handle *h, const double *f, const double *g);
 
-/* Derived lattice constants (host, n >= LBPC_L_COUNT doubles). */
+/* Derived lattice constants of the handle (host, n >= LBPC_L_COUNT doubles).  Passages:
+ * as lbpc_lattice_constants. */
 lbpc_status lbpc_get_lattice(const lbpc_handle *h, double *out, int n);
 
-/* Checkpoint of the full state (populations, h', wall fields, step) in host memory:
+/* Checkpoint of the full state (populations, h', wall fields, wall residuals, step) in
+ * host memory:
  * lbpc_state_bytes() bytes; lbpc_load requires a handle of the same shape, precision
- * and streaming.  Synchronous. */
+ * and streaming (LBPC_ERR_PARAM otherwise, or for a short buffer or a bad header).
+ * Synchronous.  Passage: none (checkpoint/restart has no counterpart in the paper). */
 size_t lbpc_state_bytes(const lbpc_handle *h);
 lbpc_status lbpc_save(lbpc_handle *h, void *host_buf, size_t bytes);
 lbpc_status lbpc_load(lbpc_handle *h, const void *host_buf, size_t bytes);
 
 /*
  * Adjoint (hand-written reverse mode of the coupled step; not in the paper, which has
- * no gradients).  Objective J = sum over nodes of f_l(h_N), the liquid volume after
+ * no gradients: it differentiates the step defined by Eq. 2, 5, 21-25, 49-56).  Objective J = sum over nodes of f_l(h_N), the liquid volume after
  * nsteps steps from the state held when lbpc_adjoint_forward is called; that state is a
  * fixed input.  Gradients: dJ/dT_w of the per-node temperature field of one isothermal
  * face (face-area values, layout of lbpc_set_wall_temperature) and dJ/dSt, where St
@@ -220,8 +256,8 @@ lbpc_status lbpc_load(lbpc_handle *h, const void *host_buf, size_t bytes);
  * over the last segment; the backward sweeps that tape backwards, then for each earlier
  * segment recomputes it from its checkpoint writing the tape (in the checkpoint slots: the
  * handle's own state is not touched), and sweeps it backwards.  The adjoint populations
- * are kept in the compute precision;
- * the parameter gradients accumulate in FP64.  Pull streaming only (LBPC_ERR_STATE
+ * are kept in the compute precision; the parameter gradients are summed per warp in the
+ * compute precision and accumulated in FP64.  Pull streaming only (LBPC_ERR_STATE
  * otherwise).  dev_ws: device, 256-byte aligned, >= lbpc_adjoint_workspace_bytes().
  *
  * lbpc_adjoint_forward advances the handle by nsteps and returns J (host);
@@ -256,10 +292,13 @@ lbpc_status lbpc_adjoint(lbpc_handle *h, int nsteps, int ckpt_every, void *dev_w
 #define LBPC_NOALLOC_MAX_NX 4096
 lbpc_status lbpc_get_scalars_noalloc(lbpc_handle *h, double *out_dev);
 
+/* Time steps of the current state; kernels this handle has launched since it was created
+ * (every launch on its stream, diagnostics and checks included); the message of the last
+ * failed call (NULL handle: of the last failed lbpc_create); release of the handle (the
+ * workspace stays the caller's).  Passage: none (bookkeeping of the interface). */
 long long lbpc_step_count(const lbpc_handle *h);
-/* Number of kernels this handle has launched since it was created. */
 long long lbpc_launch_count(const lbpc_handle *h);
-const char *lbpc_last_error(const lbpc_handle *h); /* NULL handle: last create error */
+const char *lbpc_last_error(const lbpc_handle *h);
 void lbpc_destroy(lbpc_handle *h);
 
 #ifdef __cplusplus

@@ -44,8 +44,12 @@ struct Args {
     int wall_iso[6];     // face is an isothermal wall (anti-bounce-back of g)
     int wall[6];         // face is a wall (not periodic)
     const double* Tw[6]; // per-face wall temperature fields (device)
+    float* wres[6];      // per-face FP32 residuals of the wall g populations (16-bit g and
+                         // isothermal faces only; else null)
     int flow;            // flow lattice present
     double hs, L;        // FP64 copies for the enthalpy inversion
+    long long Lbits;     // bits of L as a signed integer (branch tests of the inversion)
+    float L_below;       // largest float below (float)L (mushy values on the FP32 tape)
     Coef<float> cf;
     Coef<double> cd;
 };
@@ -90,6 +94,9 @@ struct Launchers {
                      double* Jpart, cudaStream_t);
     void (*adj_reverse)(const Args&, const void* lin, void* lout, const void* tape_e,
                         const void* tape_m, int wface, double* gtw, double* Lpart, cudaStream_t);
+    // divergence check: *flag = 1 if a stored g population or h' is not finite (the flag
+    // is not cleared here)
+    void (*check)(const Args&, const void* g, const double* hp, int* flag, cudaStream_t);
     size_t f_bytes;        // bytes of one stored f value
     size_t g_bytes;        // bytes of one stored g value
     size_t compute_bytes;  // bytes of one compute-precision value (adjoint, tape)
@@ -115,9 +122,31 @@ const Launchers& launchers_bf16();
 const Launchers& launchers_f16g32();
 const Launchers& launchers_bf16g32();
 
-void finalize_reduction(const Args& a, const double* partial, const double* lines,
-                        const double* face_area_inv, double nu_scale, double fd_scale,
-                        double step, double* result, double* hist_row, int hist_write,
-                        cudaStream_t s);
+// Second stage of the diagnostics, one block on stream s: fixed-order sums of the
+// RED_BLOCKS x NRED block partials and the LBPC_S_* scalars into result[LBPC_S_COUNT]
+// (and into hist_row when it is not null).  lines: the three front lines of nx values.
+cudaError_t finalize_reduction(const double* partial, const double* lines, int nx, double area,
+                               double nu_scale, double fd_scale, double step, int flow, int iso0,
+                               double* result, double* hist_row, cudaStream_t s);
 
 }  // namespace lbpc
+
+// Read-only view of a handle for lbpc_noalloc.cu (the handle's layout stays private to
+// lbpc_api.cu).  view() also makes the handle's device current; count_launches() adds n
+// to the handle's launch count.
+namespace lbpc_noalloc_access {
+struct View {
+    const lbpc::Launchers* L;
+    const lbpc::Args* args;
+    lbpc::Layout layout;
+    const void* f;
+    const void* g;
+    const double* hp;
+    int nx, ny, nz, device, flow, iso0;
+    double nu_scale, fd_scale, step;
+    cudaStream_t stream;
+};
+lbpc_status view(lbpc_handle* h, View* v);
+void set_error(lbpc_handle* h, const char* msg);
+void count_launches(lbpc_handle* h, int n);
+}  // namespace lbpc_noalloc_access

@@ -13,6 +13,7 @@
 #include <stdint.h>
 
 #include <cmath>
+#include <cstring>
 
 #include "lbpc_internal.h"
 
@@ -77,7 +78,9 @@ template <int P> using CT = typename Store<Mode<P>::F>::C;
 
 // Exact float -> double by integer operations (subnormal floats, below 1.2e-38, become
 // zero); keeps the conversions off the FP64 pipe, which on GB300 issues a few
-// operations per clock per SM.
+// operations per clock per SM.  Float infinities and NaN map to finite doubles, so a
+// non-finite population does not reach the FP64 rest channel: divergence checks look at
+// the populations themselves (macro_node, k_check).
 LBPC_HD double f2d_exact(float v) {
 #if defined(__CUDA_ARCH__)
     const unsigned u = __float_as_uint(v);
@@ -90,21 +93,35 @@ LBPC_HD double f2d_exact(float v) {
     return (float)v == 0.0f || std::fabs(v) < 1.17549435e-38f ? 0.0 : (double)v;
 #endif
 }
-// double -> float rounding toward zero by integer operations (|v| below 2^-126 gives 0).
-LBPC_HD float d2f_trunc(double v) {
+// double -> float rounded to nearest (ties to even) by integer operations, off the FP64
+// pipe: half an ulp of the result is added to the magnitude (less one unless the kept
+// last bit is odd) and the exponent is rebiased.  Results below 2^-126 become signed
+// zero; NaN stays NaN, values beyond the float range become infinities.
+LBPC_HD float d2f_rn(double v) {
 #if defined(__CUDA_ARCH__)
     const unsigned long long u = (unsigned long long)__double_as_longlong(v);
-    const int ex = (int)((u >> 52) & 0x7ff) - 896;  // float biased exponent
+    const unsigned long long mag = u & 0x7fffffffffffffffull;
     const unsigned sign = (unsigned)(u >> 63) << 31;
+    const unsigned long long r = mag + 0x0fffffffull + ((mag >> 29) & 1ull);
+    const int ex = (int)(r >> 52) - 896;  // float biased exponent
     if (ex <= 0) return __uint_as_float(sign);
-    if (ex >= 255) return __uint_as_float(sign | 0x7f800000u);
-    return __uint_as_float(sign | ((unsigned)ex << 23) | (unsigned)((u >> 29) & 0x7fffffu));
+    if (ex >= 255)
+        return __uint_as_float(sign | (mag > 0x7ff0000000000000ull ? 0x7fc00000u : 0x7f800000u));
+    return __uint_as_float(sign | (unsigned)((r >> 29) - (896ull << 23)));
 #else
-    const double a = std::fabs(v);
-    if (a < 1.1754943508222875e-38) return std::signbit(v) ? -0.0f : 0.0f;
-    float r = (float)v;
-    if (std::fabs((double)r) > a) r = std::nextafter(r, 0.0f);  // toward zero
-    return r;
+    if (std::fabs(v) < 1.1754943508222875e-38) return std::signbit(v) ? -0.0f : 0.0f;
+    return (float)v;
+#endif
+}
+// Bits of a double as a signed integer: for a positive bound B, v <= 0 and v >= B (v not
+// NaN) are the integer tests bits(v) <= 0 and bits(v) >= bits(B).
+LBPC_HD long long dbits(double v) {
+#if defined(__CUDA_ARCH__)
+    return __double_as_longlong(v);
+#else
+    long long b;
+    std::memcpy(&b, &v, sizeof b);
+    return b;
 #endif
 }
 
@@ -305,10 +322,18 @@ LBPC_HD void gather_f(const Args& a, const NB& b, int n,
 
 // g_1..6 (g[0] is not gathered: the rest population is the FP64 channel h').  The g
 // lattice holds six planes: population q lives in plane q - 1.
+//
+// Wall residuals (16-bit g): a population that crosses an isothermal face is kept to FP32
+// precision, as its 16-bit stored value plus the FP32 residual in a per-face array wres[f]
+// (one value per boundary node): the outgoing post-collision population in the pull and
+// the swapped AA layout, the incoming pre-collision one in the natural AA layout.  The
+// anti-bounce-back value -(g*_out + rho) + omega_T Cp_ref T_w is returned split into a
+// part on the 2^-20 grid (g[q]) and an FP32 remainder (lo[q]), so that e = e' + sum g +
+// sum lo stays exact; the wall flux then carries no 16-bit rounding.  lo must start at 0.
 template <int P, int LAYOUT, bool NC, class NB>
 LBPC_HD void gather_g(const Args& a, const NB& b, int n, int x, int y, int z,
-                                         const typename Store<P>::T* gs,
-                                         typename Store<P>::C* g) {
+                      const typename Store<P>::T* gs, typename Store<P>::C* g,
+                      typename Store<P>::C* lo) {
     using S = Store<P>;
     using C = typename S::C;
     const Coef<C>& k = coef<C>(a);
@@ -316,15 +341,28 @@ LBPC_HD void gather_g(const Args& a, const NB& b, int n, int x, int y, int z,
 #define LBPC_GG(q, ex, ey, ez, op)                                                       \
     {                                                                                   \
         if constexpr (LAYOUT == LAYOUT_AA_NATURAL) {                                    \
-            g[q] = S::dec(ldv<P, LAYOUT, NC>(gs + (size_t)(q - 1) * N + n), k.gshift);         \
+            g[q] = S::dec(ldv<P, LAYOUT, NC>(gs + (size_t)(q - 1) * N + n), k.gshift);  \
+            if constexpr (S::kGrid) {                                                   \
+                if (b.template wall<ex, ey, ez>() && a.wall_iso[q - 1])                  \
+                    lo[q] = a.wres[q - 1][face_index(a, q - 1, x, y, z)];               \
+            }                                                                           \
         } else {                                                                        \
-            const bool w = b.template wall<ex, ey, ez>();                                      \
-            const int idx = w ? n : n + b.template off<ex, ey, ez>();                          \
+            const bool w = b.template wall<ex, ey, ez>();                               \
+            const int idx = w ? n : n + b.template off<ex, ey, ez>();                   \
             int slot;                                                                   \
-            if constexpr (LAYOUT == LAYOUT_PULL) slot = w ? op : q;                      \
+            if constexpr (LAYOUT == LAYOUT_PULL) slot = w ? op : q;                     \
             else slot = w ? q : op;                                                     \
-            C v = S::dec(ldv<P, LAYOUT, NC>(gs + (size_t)(slot - 1) * N + idx), k.gshift);     \
-            if (w && a.wall_iso[q - 1]) v = S::grid(-v + abb_source(a, k, q - 1, x, y, z)); \
+            C v = S::dec(ldv<P, LAYOUT, NC>(gs + (size_t)(slot - 1) * N + idx), k.gshift); \
+            if (w && a.wall_iso[q - 1]) {                                               \
+                const C src = abb_source(a, k, q - 1, x, y, z);                         \
+                if constexpr (S::kGrid) {                                               \
+                    const C hi = S::grid(src);                                          \
+                    lo[q] = (src - hi) - a.wres[q - 1][face_index(a, q - 1, x, y, z)];  \
+                    v = hi - v;                                                         \
+                } else {                                                                \
+                    v = S::grid(src - v);                                               \
+                }                                                                       \
+            }                                                                           \
             g[q] = v;                                                                   \
         }                                                                               \
     }
@@ -361,32 +399,51 @@ LBPC_HD void scatter_f(const Args& a, const NB& b, int n,
 }
 
 // Stores g*_1..6 and replaces g[a] by the value as stored (rounded to the storage
-// precision), which is what the downwind neighbours will read.
+// precision), which is what the downwind neighbours will read.  16-bit g: a population
+// leaving through an isothermal face also leaves its residual (g* minus the stored value)
+// in wres and in lo[q], which the rest channel accounts for; in the odd AA step the
+// incoming anti-bounce-back value is formed from the unrounded g* and its own residual
+// kept.  lo must start at 0.
 template <int P, int KIND, class NB>
 LBPC_HD void scatter_g(const Args& a, const NB& b, int n, int x, int y, int z,
-                       typename Store<P>::T* gd, typename Store<P>::C* g) {
+                       typename Store<P>::T* gd, typename Store<P>::C* g,
+                       typename Store<P>::C* lo) {
     using S = Store<P>;
     using C = typename S::C;
     const Coef<C>& k = coef<C>(a);
     const size_t N = (size_t)a.N;
 #define LBPC_SG(q, ex, ey, ez, op)                                                       \
     {                                                                                   \
-        const auto v = S::enc_g(g[q], k.gshift);                                        \
+        const C val = g[q];                                                             \
+        const auto v = S::enc_g(val, k.gshift);                                         \
         g[q] = S::dec(v, k.gshift);                                                     \
-        if constexpr (KIND == STEP_PULL) {                                              \
-            gd[(size_t)(q - 1) * N + n] = v;                                                  \
-        } else if constexpr (KIND == STEP_AA_EVEN) {                                    \
-            gd[(size_t)(op - 1) * N + n] = v;                                                 \
+        const bool w = b.template wall<-(ex), -(ey), -(ez)>();                          \
+        const bool iso = w && a.wall_iso[op - 1];                                       \
+        if constexpr (S::kGrid) {                                                       \
+            if (iso) lo[q] = val - g[q];                                                \
+        }                                                                               \
+        if constexpr (KIND == STEP_PULL || KIND == STEP_AA_EVEN) {                      \
+            gd[(size_t)((KIND == STEP_PULL ? q : op) - 1) * N + n] = v;                 \
+            if constexpr (S::kGrid) {                                                   \
+                if (iso) a.wres[op - 1][face_index(a, op - 1, x, y, z)] = lo[q];        \
+            }                                                                           \
         } else {                                                                        \
-            const bool w = b.template wall<-(ex), -(ey), -(ez)>();                             \
             if (w) {                                                                    \
                 auto vb = v;                                                            \
-                if (a.wall_iso[op - 1])                                                 \
-                    vb = S::enc_g(-S::dec(v, k.gshift) + abb_source(a, k, op - 1, x, y, z), \
-                                  k.gshift);                                            \
-                gd[(size_t)(op - 1) * N + n] = vb;                                            \
+                if (iso) {                                                              \
+                    const C src = abb_source(a, k, op - 1, x, y, z);                    \
+                    if constexpr (S::kGrid) {                                           \
+                        const C in = src - val;                                         \
+                        vb = S::enc_g(in, k.gshift);                                    \
+                        a.wres[op - 1][face_index(a, op - 1, x, y, z)] =                \
+                            in - S::dec(vb, k.gshift);                                  \
+                    } else {                                                            \
+                        vb = S::enc_g(src - g[q], k.gshift);                            \
+                    }                                                                   \
+                }                                                                       \
+                gd[(size_t)(op - 1) * N + n] = vb;                                      \
             } else {                                                                    \
-                gd[(size_t)(q - 1) * N + n + b.template off<-(ex), -(ey), -(ez)>()] = v;             \
+                gd[(size_t)(q - 1) * N + n + b.template off<-(ex), -(ey), -(ez)>()] = v; \
             }                                                                           \
         }                                                                               \
     }
@@ -394,29 +451,107 @@ LBPC_HD void scatter_g(const Args& a, const NB& b, int n, int x, int y, int z,
 #undef LBPC_SG
 }
 
+// Anti-bounce-back value of the g population entering through isothermal face `face` at
+// a boundary node, from the stored outgoing value v (representation): 32-bit g gives it
+// directly; 16-bit g adds the outgoing residual and splits the result into the grid part
+// (returned) and the remainder (lo), as gather_g does.
+template <int PG>
+LBPC_HD float wall_in(const Args& a, const Coef<float>& k, int face, int x, int y, int z,
+                      float v, float& lo) {
+    using S = Store<PG>;
+    const float src = abb_source(a, k, face, x, y, z);
+    if constexpr (S::kGrid) {
+        const float hi = S::grid(src);
+        lo = (src - hi) - a.wres[face][face_index(a, face, x, y, z)];
+        return hi - v;
+    } else {
+        return S::grid(src - v);
+    }
+}
+// 16-bit g: residual of a population leaving through x face `face` (its post-collision
+// value minus the value stored), written to the face's residual array; returns it as
+// the FP64 amount the rest channel gives up besides the stored value.
+template <int PG>
+LBPC_HD double wall_out(const Args& a, int face, int y, int z, float val, float stored) {
+    const float r = val - stored;
+    a.wres[face][y + a.ny * z] = r;
+    return f2d_exact(r);
+}
+
+// Odd AA step: the stored anti-bounce-back value that enters through isothermal x face
+// `face` for the next (even) step, from the unrounded outgoing population out (v: its
+// stored value, the rounded form used by 32-bit g); 16-bit g keeps its residual in wres.
+template <int PG>
+LBPC_HD typename Store<PG>::T wall_in_aa(const Args& a, const Coef<float>& k, int face, int x,
+                                         int y, int z, float out, typename Store<PG>::T v) {
+    using S = Store<PG>;
+    const float src = abb_source(a, k, face, x, y, z);
+    if constexpr (S::kGrid) {
+        const float in = src - out;
+        const auto vb = S::enc_g(in, k.gshift);
+        a.wres[face][y + a.ny * z] = in - S::dec(vb, k.gshift);
+        return vb;
+    } else {
+        return S::enc_g(src - S::dec(v, k.gshift), k.gshift);
+    }
+}
+
+// Sum of the FP32 wall remainders lo[1..6] added to (sign +1) or taken from (-1) an FP64
+// value, one exact FP64 addition per nonzero remainder.
+template <int P>
+LBPC_HD double add_lo(double v, const typename Store<P>::C* lo, double sign) {
+    if constexpr (Store<P>::kGrid) {
+#pragma unroll
+        for (int q = 1; q < 7; q++)
+            if (lo[q] != 0.0f) v += sign * f2d_exact(lo[q]);
+    }
+    return v;
+}
+
 // ---------------------------------------------------------------------------------
 // Local physics.
 // ---------------------------------------------------------------------------------
 
 // Eq. 2 inverted (h = C_p T + f_l L; solid for h <= h_s, liquid for h >= h_s + L, mushy
-// at T_m in between), from the FP64 enthalpy excess e = h - h_s that the rest channel
-// carries, so that the cancelling subtraction near the melting point is exact.
-LBPC_HD float to_compute(double v, float) { return d2f_trunc(v); }
-LBPC_HD double to_compute(double v, double) { return v; }
-
-template <class C>
-LBPC_HD void invert_excess(const Coef<C>& k, double e, C& T, C& fl) {
-    const C d = to_compute(e, C(0));
-    if (d <= C(0)) {
-        fl = C(0);
-        T = k.Tm + d * k.Cps_inv;
-    } else if (d >= k.L) {
-        fl = C(1);
-        T = k.Tm + (d - k.L) * k.Cpl_inv;
+// at T_m in between) from the FP64 enthalpy excess e = h - h_s that the rest channel
+// carries, so that the cancelling subtraction near the melting point is exact.  FP64
+// storage computes everything in FP64, and so do the reported fields and diagnostics in
+// every mode.  For the FP32 collision of the 32/16-bit modes the branch is still decided
+// on the FP64 excess, exactly, by integer tests on its bits (off the FP64 pipe); the value
+// is formed in FP32 from e rounded once to nearest: T_m + d / C_p,s, T_m + (d - L) / C_p,l
+// or d / L with d = rn(e), which is within half an FP32 ulp of e (over C_p) of the FP64
+// value (an FP64 fused multiply-add per node here cost 5% of the 16-bit step's throughput).
+LBPC_HD void invert_excess(const Args& a, double e, double& T, double& fl) {
+    const Coef<double>& k = a.cd;
+    if (e <= 0.0) {
+        fl = 0.0;
+        T = k.Tm + e * k.Cps_inv;
+    } else if (e >= k.L) {
+        fl = 1.0;
+        T = k.Tm + (e - k.L) * k.Cpl_inv;
     } else {
-        fl = d * k.L_inv;
+        fl = e * k.L_inv;
         T = k.Tm;
     }
+}
+LBPC_HD void invert_excess(const Args& a, double e, float& T, float& fl) {
+    const long long b = dbits(e);
+    const bool solid = b <= 0, liquid = b >= a.Lbits;
+    const float d = d2f_rn(e);
+    const Coef<float>& k = a.cf;
+    T = solid ? k.Tm + d * k.Cps_inv : (liquid ? k.Tm + (d - k.L) * k.Cpl_inv : k.Tm);
+    fl = solid ? 0.0f : (liquid ? 1.0f : fminf(d * k.L_inv, 1.0f));
+}
+
+// The excess taped for the adjoint, in the compute precision: e itself (FP64), or e
+// rounded to nearest and kept strictly inside (0, L) on the mushy branch, so that the
+// reverse sweep's branch tests in FP32 take the branch the forward took in FP64.
+LBPC_HD double tape_excess(const Args&, double e, double) { return e; }
+LBPC_HD float tape_excess(const Args& a, double e, float) {
+    const long long b = dbits(e);
+    const float r = d2f_rn(e);
+    if (b > 0 && b < a.Lbits) return fminf(fmaxf(r, 1.17549435e-38f), a.L_below);
+    return r;
 }
 
 // Velocity factor phi of the solid closure, u = phi u*, F_s = -2 (1 - phi) rho0 u*: the
@@ -698,23 +833,30 @@ LBPC_HD void step_node(const Args& a, int x, int y, int z, const TF<P>* fs,
     const NbInterior bi{a.nx, a.nx * a.ny};
     const Nb b = make_nb(a, x, y, z);
 
-    C f[19], g[7];
+    C f[19], g[7], lo[7] = {};
     if (interior) {
         if constexpr (FLOW) gather_f<Mode<P>::F, LAYOUT, NC>(a, bi, n, fs, f);
-        gather_g<Mode<P>::G, LAYOUT, NC>(a, bi, n, x, y, z, gs, g);
+        gather_g<Mode<P>::G, LAYOUT, NC>(a, bi, n, x, y, z, gs, g, lo);
     } else {
         if constexpr (FLOW) gather_f<Mode<P>::F, LAYOUT, NC>(a, b, n, fs, f);
-        gather_g<Mode<P>::G, LAYOUT, NC>(a, b, n, x, y, z, gs, g);
+        gather_g<Mode<P>::G, LAYOUT, NC>(a, b, n, x, y, z, gs, g, lo);
     }
-    const double e = excess_plus<Mode<P>::G>(hp[n], g);  // h - h_s
+    // h - h_s; with wall remainders (16-bit g) the collision sees the full FP32 values
+    const double e = add_lo<Mode<P>::G>(excess_plus<Mode<P>::G>(hp[n], g), lo, 1.0);
+    if constexpr (Store<Mode<P>::G>::kGrid) {
+        for (int q = 1; q < 7; q++) {
+            g[q] += lo[q];
+            lo[q] = C(0);
+        }
+    }
 
     C T, fl;
-    invert_excess(k, e, T, fl);
+    invert_excess(a, e, T, fl);
     C ux = C(0), uy = C(0), uz = C(0), rho = C(0), jx = C(0), jy = C(0), jz = C(0);
     if constexpr (FLOW)  // FLOW 2: the drag closure, phi(f_l) in place of f_l
         collide_flow(f, k, T, FLOW == 2 ? darcy_phi(k, fl) : fl, ux, uy, uz, rho, jx, jy, jz);
     if constexpr (TAPE) {  // macroscopic tape of the pre-collision state (adjoint)
-        tape_e[n] = to_compute(e, C(0));  // what the inversion uses
+        tape_e[n] = tape_excess(a, e, C(0));
         if constexpr (FLOW) {
             tape_m[n] = rho;
             tape_m[(size_t)a.N + n] = jx;
@@ -725,12 +867,12 @@ LBPC_HD void step_node(const Args& a, int x, int y, int z, const TF<P>* fs,
     collide_enth<C, !FLOW>(g, k, T, fl, ux, uy, uz);
     if (interior) {
         if constexpr (FLOW) scatter_f<Mode<P>::F, KIND>(a, bi, n, fd, f);
-        scatter_g<Mode<P>::G, KIND>(a, bi, n, x, y, z, gd, g);
+        scatter_g<Mode<P>::G, KIND>(a, bi, n, x, y, z, gd, g, lo);
     } else {
         if constexpr (FLOW) scatter_f<Mode<P>::F, KIND>(a, b, n, fd, f);
-        scatter_g<Mode<P>::G, KIND>(a, b, n, x, y, z, gd, g);
+        scatter_g<Mode<P>::G, KIND>(a, b, n, x, y, z, gd, g, lo);
     }
-    hp[n] = excess_minus<Mode<P>::G>(e, g);
+    hp[n] = add_lo<Mode<P>::G>(excess_minus<Mode<P>::G>(e, g), lo, -1.0);
 }
 
 
@@ -744,8 +886,8 @@ LBPC_HD void pair_collide(const Args& a, CT<P>* f0, CT<P>* f1, CT<P>* g0, CT<P>*
     using VC = typename Vec2<C>::type;
     const Coef<C>& k = coef<C>(a);
     C T0, fl0, T1, fl1;
-    invert_excess(k, e0, T0, fl0);
-    invert_excess(k, e1, T1, fl1);
+    invert_excess(a, e0, T0, fl0);
+    invert_excess(a, e1, T1, fl1);
     C ux0 = C(0), uy0 = C(0), uz0 = C(0), ux1 = C(0), uy1 = C(0), uz1 = C(0);
     if constexpr (FLOW) {
         C r0, jx0, jy0, jz0, r1, jx1, jy1, jz1;
@@ -762,7 +904,7 @@ LBPC_HD void pair_collide(const Args& a, CT<P>* f0, CT<P>* f1, CT<P>* g0, CT<P>*
         }
     }
     if constexpr (TAPE)
-        *reinterpret_cast<VC*>(tape_e + n0) = VC{to_compute(e0, C(0)), to_compute(e1, C(0))};
+        *reinterpret_cast<VC*>(tape_e + n0) = VC{tape_excess(a, e0, C(0)), tape_excess(a, e1, C(0))};
     collide_enth<C, !FLOW>(g0, k, T0, fl0, ux0, uy0, uz0);
     collide_enth<C, !FLOW>(g1, k, T1, fl1, ux1, uy1, uz1);
 }
@@ -772,11 +914,13 @@ LBPC_HD void pair_collide(const Args& a, CT<P>* f0, CT<P>* f1, CT<P>* g0, CT<P>*
 // rules (periodic wrap; at a wall the reflected population of the node itself) applied
 // by selecting a 32-bit element offset from the population's plane on the lanes at x = 0
 // / x = nx - 1; every store is a pair.  Requires even nx.
+// xwall (16-bit g): some lane of the warp owns a node on an isothermal x wall; the wall
+// work of the other warps is then skipped by a warp-uniform branch.
 template <int P, int FLOW, bool TAPE = false>
 LBPC_HD void step_pair_pull(const Args& a, int x0, int y, int z, const TF<P>* fs,
                             TF<P>* fd, const TG<P>* gs,
                             TG<P>* gd, double* hp, CT<P>* tape_e = nullptr,
-                            CT<P>* tape_m = nullptr) {
+                            CT<P>* tape_m = nullptr, bool xwall = false) {
     using SF = Store<Mode<P>::F>;
     using SG = Store<Mode<P>::G>;
     using TFt = typename SF::T;
@@ -793,6 +937,9 @@ LBPC_HD void step_pair_pull(const Args& a, int x0, int y, int z, const TF<P>* fs
     const int n0 = x0 + a.nx * (y + a.ny * z), n1 = n0 + 1;
     const bool xlo = x0 == 0, xhi = x0 + 1 == a.nx - 1;
     const bool wlo = xlo && a.wall[0], whi = xhi && a.wall[1];
+    const bool iso0 = wlo && a.wall_iso[0], iso1 = whi && a.wall_iso[1];
+    const bool wwarp = !SG::kGrid || xwall;  // 16-bit g: wall work only in wall warps
+    C lo0 = C(0), lo1 = C(0);  // wall remainders of the incoming g (16-bit g)
     // upwind x-neighbour of node 0 for e_x = +1 and of node 1 for e_x = -1 (with wrap)
     const int up0 = xlo ? n0 + a.nx - 1 : n0 - 1;
     const int up1 = xhi ? n1 - (a.nx - 1) : n1 + 1;
@@ -829,13 +976,13 @@ LBPC_HD void step_pair_pull(const Args& a, int x0, int y, int z, const TF<P>* fs
         } else if constexpr ((ex) == 1) {                                               \
             const int i0 = wlo ? ((op) - (q)) * N32 + n0 : up0 + oyz;                   \
             C v = SG::dec(ldv<Mode<P>::G, LAYOUT_PULL, true>(pl + i0), k.gshift);                 \
-            if (wlo && a.wall_iso[0]) v = SG::grid(-v + abb_source(a, k, 0, x0, y, z)); \
+            if (wwarp && iso0) v = wall_in<Mode<P>::G>(a, k, 0, x0, y, z, v, lo0);      \
             g0[q] = v;                                                                  \
             g1[q] = SG::dec(ldv<Mode<P>::G, LAYOUT_PULL, true>(pl + n0 + oyz), k.gshift);         \
         } else {                                                                        \
             const int i1 = whi ? ((op) - (q)) * N32 + n1 : up1 + oyz;                   \
             C v = SG::dec(ldv<Mode<P>::G, LAYOUT_PULL, true>(pl + i1), k.gshift);                 \
-            if (whi && a.wall_iso[1]) v = SG::grid(-v + abb_source(a, k, 1, x0 + 1, y, z)); \
+            if (wwarp && iso1) v = wall_in<Mode<P>::G>(a, k, 1, x0 + 1, y, z, v, lo1);  \
             g1[q] = v;                                                                  \
             g0[q] = SG::dec(ldv<Mode<P>::G, LAYOUT_PULL, true>(pl + n1 + oyz), k.gshift);         \
         }                                                                               \
@@ -843,8 +990,15 @@ LBPC_HD void step_pair_pull(const Args& a, int x0, int y, int z, const TF<P>* fs
     LBPC_Q7(LBPC_PG)
 #undef LBPC_PG
     const double2 ep = ld_any<true>(reinterpret_cast<const double2*>(hp + n0));
-    const double e0 = excess_plus<Mode<P>::G>(ep.x, g0), e1 = excess_plus<Mode<P>::G>(ep.y, g1);
+    double e0 = excess_plus<Mode<P>::G>(ep.x, g0), e1 = excess_plus<Mode<P>::G>(ep.y, g1);
+    if constexpr (SG::kGrid) {  // the wall remainders (16-bit g): exact FP64 additions
+        if (xwall) {
+            if (iso0) { e0 += f2d_exact(lo0); g0[1] += lo0; }
+            if (iso1) { e1 += f2d_exact(lo1); g1[2] += lo1; }
+        }
+    }
     pair_collide<P, FLOW, TAPE>(a, f0, f1, g0, g1, e0, e1, n0, tape_e, tape_m);
+    const C out0 = g0[2], out1 = g1[1];  // populations leaving through the x walls
     if constexpr (FLOW) {
 #define LBPC_SPF(q, ex, ey, ez, op)                                                      \
         *reinterpret_cast<VF*>(fd + (size_t)q * N + n0) = PRF::enc(f0[q], f1[q], fshift(k, q));
@@ -859,7 +1013,14 @@ LBPC_HD void step_pair_pull(const Args& a, int x0, int y, int z, const TF<P>* fs
     }
     LBPC_Q7(LBPC_SPG)
 #undef LBPC_SPG
-    *reinterpret_cast<double2*>(hp + n0) = make_double2(excess_minus<Mode<P>::G>(e0, g0), excess_minus<Mode<P>::G>(e1, g1));
+    double h0n = excess_minus<Mode<P>::G>(e0, g0), h1n = excess_minus<Mode<P>::G>(e1, g1);
+    if constexpr (SG::kGrid) {  // residuals of the populations leaving through the x walls
+        if (xwall) {
+            if (iso0) h0n -= wall_out<Mode<P>::G>(a, 0, y, z, out0, g0[2]);
+            if (iso1) h1n -= wall_out<Mode<P>::G>(a, 1, y, z, out1, g1[1]);
+        }
+    }
+    *reinterpret_cast<double2*>(hp + n0) = make_double2(h0n, h1n);
 }
 
 
@@ -882,7 +1043,8 @@ LBPC_HD void opaque(T& v) {
 // f*_q goes to slot q at x + e_q (slot qbar at x behind a wall), with the wall rules of the
 // per-node path.  Each thread reads and writes the same set of slots, so in place is safe.
 template <int P, int FLOW, bool ODD>
-LBPC_HD void step_pair_aa(const Args& a, int x0, int y, int z, TF<P>* F, TG<P>* G, double* hp) {
+LBPC_HD void step_pair_aa(const Args& a, int x0, int y, int z, TF<P>* F, TG<P>* G, double* hp,
+                          bool xwall = false) {
     using SF = Store<Mode<P>::F>;
     using SG = Store<Mode<P>::G>;
     using TFt = typename SF::T;
@@ -899,6 +1061,9 @@ LBPC_HD void step_pair_aa(const Args& a, int x0, int y, int z, TF<P>* F, TG<P>* 
     const int n0 = x0 + a.nx * (y + a.ny * z), n1 = n0 + 1;
     const bool xlo = x0 == 0, xhi = x0 + 1 == a.nx - 1;
     const bool wlo = xlo && a.wall[0], whi = xhi && a.wall[1];
+    const bool iso0 = wlo && a.wall_iso[0], iso1 = whi && a.wall_iso[1];
+    const bool wwarp = !SG::kGrid || xwall;  // 16-bit g: wall work only in wall warps
+    C lo0 = C(0), lo1 = C(0);  // wall remainders of the incoming g (16-bit g)
     const int dn0 = xlo ? n0 + a.nx - 1 : n0 - 1;      // x-neighbour x0 - 1 (wrapped)
     const int up1 = xhi ? n1 - (a.nx - 1) : n1 + 1;    // x-neighbour x1 + 1 (wrapped)
     C f0[19], f1[19], g0[7], g1[7];
@@ -937,13 +1102,13 @@ LBPC_HD void step_pair_aa(const Args& a, int x0, int y, int z, TF<P>* F, TG<P>* 
                 PRG::dec(*reinterpret_cast<const VG*>(sw + n0 + oyz), k.gshift, g0[q], g1[q]); \
             } else if constexpr ((ex) == 1) {                                           \
                 C v = SG::dec(sw[wlo ? ((q) - (op)) * N32 + n0 : dn0 + oyz], k.gshift);  \
-                if (wlo && a.wall_iso[0]) v = SG::grid(-v + abb_source(a, k, 0, x0, y, z)); \
+                if (wwarp && iso0) v = wall_in<Mode<P>::G>(a, k, 0, x0, y, z, v, lo0);  \
                 g0[q] = v;                                                              \
                 g1[q] = SG::dec(sw[n0 + oyz], k.gshift);                                    \
             } else {                                                                    \
                 g0[q] = SG::dec(sw[n1 + oyz], k.gshift);                                    \
                 C v = SG::dec(sw[whi ? ((q) - (op)) * N32 + n1 : up1 + oyz], k.gshift);  \
-                if (whi && a.wall_iso[1]) v = SG::grid(-v + abb_source(a, k, 1, x0 + 1, y, z)); \
+                if (wwarp && iso1) v = wall_in<Mode<P>::G>(a, k, 1, x0 + 1, y, z, v, lo1); \
                 g1[q] = v;                                                              \
             }                                                                           \
         }                                                                               \
@@ -951,8 +1116,19 @@ LBPC_HD void step_pair_aa(const Args& a, int x0, int y, int z, TF<P>* F, TG<P>* 
     LBPC_Q7(LBPC_AGG)
 #undef LBPC_AGG
     const double2 ep = *reinterpret_cast<const double2*>(hp + n0);
-    const double e0 = excess_plus<Mode<P>::G>(ep.x, g0), e1 = excess_plus<Mode<P>::G>(ep.y, g1);
+    double e0 = excess_plus<Mode<P>::G>(ep.x, g0), e1 = excess_plus<Mode<P>::G>(ep.y, g1);
+    if constexpr (SG::kGrid) {  // the wall remainders (16-bit g): exact FP64 additions
+        if (xwall) {
+            if constexpr (!ODD) {  // natural layout: the incoming populations' own residuals
+                if (iso0) lo0 = a.wres[0][y + a.ny * z];
+                if (iso1) lo1 = a.wres[1][y + a.ny * z];
+            }
+            if (iso0) { e0 += f2d_exact(lo0); g0[1] += lo0; }
+            if (iso1) { e1 += f2d_exact(lo1); g1[2] += lo1; }
+        }
+    }
     pair_collide<P, FLOW>(a, f0, f1, g0, g1, e0, e1);
+    const C out0 = g0[2], out1 = g1[1];  // populations leaving through the x walls
     // fresh copies of the indices and bases for the scatter (see opaque())
     int m0 = n0, mdn = dn0, mup = up1, tsy = sy, tsz = sz;
     TF<P>* Fw = F;
@@ -999,16 +1175,14 @@ LBPC_HD void step_pair_aa(const Args& a, int x0, int y, int z, TF<P>* F, TG<P>* 
                 const TGt v0 = SG::enc_g(g0[q], k.gshift), v1 = SG::enc_g(g1[q], k.gshift); \
                 dq[(m0 + 1) + o2] = v0;                                                 \
                 TGt vb = v1;                                                            \
-                if (whi && a.wall_iso[1])                                               \
-                    vb = SG::enc_g(-SG::dec(v1, k.gshift) + abb_source(a, k, 1, x0 + 1, y, z), k.gshift); \
+                if (wwarp && iso1) vb = wall_in_aa<Mode<P>::G>(a, k, 1, x0 + 1, y, z, out1, v1); \
                 dq[whi ? ((op) - (q)) * N32 + (m0 + 1) : mup + o2] = vb;                \
                 g0[q] = SG::dec(v0, k.gshift);                                          \
                 g1[q] = SG::dec(v1, k.gshift);                                          \
             } else {                                                                    \
                 const TGt v0 = SG::enc_g(g0[q], k.gshift), v1 = SG::enc_g(g1[q], k.gshift); \
                 TGt vb = v0;                                                            \
-                if (wlo && a.wall_iso[0])                                               \
-                    vb = SG::enc_g(-SG::dec(v0, k.gshift) + abb_source(a, k, 0, x0, y, z), k.gshift); \
+                if (wwarp && iso0) vb = wall_in_aa<Mode<P>::G>(a, k, 0, x0, y, z, out0, v0); \
                 dq[wlo ? ((op) - (q)) * N32 + m0 : mdn + o2] = vb;                      \
                 dq[m0 + o2] = v1;                                                       \
                 g0[q] = SG::dec(v0, k.gshift);                                          \
@@ -1018,8 +1192,19 @@ LBPC_HD void step_pair_aa(const Args& a, int x0, int y, int z, TF<P>* F, TG<P>* 
     }
     LBPC_Q7(LBPC_ASG)
 #undef LBPC_ASG
-    *reinterpret_cast<double2*>(hp + n0) =
-        make_double2(excess_minus<Mode<P>::G>(e0, g0), excess_minus<Mode<P>::G>(e1, g1));
+    double h0n = excess_minus<Mode<P>::G>(e0, g0), h1n = excess_minus<Mode<P>::G>(e1, g1);
+    if constexpr (SG::kGrid) {  // residuals of the populations leaving through the x walls
+        if (xwall) {
+            if constexpr (ODD) {  // (the incoming values' residuals are in wres already)
+                if (iso0) h0n -= f2d_exact(out0 - g0[2]);
+                if (iso1) h1n -= f2d_exact(out1 - g1[1]);
+            } else {
+                if (iso0) h0n -= wall_out<Mode<P>::G>(a, 0, y, z, out0, g0[2]);
+                if (iso1) h1n -= wall_out<Mode<P>::G>(a, 1, y, z, out1, g1[1]);
+            }
+        }
+    }
+    *reinterpret_cast<double2*>(hp + n0) = make_double2(h0n, h1n);
 }
 
 // Macroscopic state of node n and its contributions to the diagnostics sums
@@ -1032,40 +1217,44 @@ LBPC_HD void macro_node(const Args& a, int n, const TF<P>* fs,
     const Coef<C>& k = coef<C>(a);
     const int x = n % a.nx, y = (n / a.nx) % a.ny, z = n / (a.nx * a.ny);
     const Nb b = make_nb(a, x, y, z);
-    C f[19], g[7];
+    C f[19], g[7], lo[7] = {};
     if constexpr (FLOW) gather_f<Mode<P>::F, LAYOUT, true>(a, b, n, fs, f);
-    gather_g<Mode<P>::G, LAYOUT, true>(a, b, n, x, y, z, gs, g);
-    const double e = excess_plus<Mode<P>::G>(hp[n], g);
+    gather_g<Mode<P>::G, LAYOUT, true>(a, b, n, x, y, z, gs, g, lo);
+    const double e = add_lo<Mode<P>::G>(excess_plus<Mode<P>::G>(hp[n], g), lo, 1.0);
     const double h = a.hs + e;
-    C T, fl;
-    invert_excess(k, e, T, fl);
+    double Td, fld;  // reported: the FP64 inversion
+    invert_excess(a, e, Td, fld);
     C rho = C(0), ux = C(0), uy = C(0), uz = C(0);
-    if constexpr (FLOW) {
-        C jx, jy, jz, Fx, Fy, Fz;
+    if constexpr (FLOW) {  // the velocity as the step computes it
+        C T, fl, jx, jy, jz, Fx, Fy, Fz;
+        invert_excess(a, e, T, fl);
         flow_macro(f, k, T, fl, rho, jx, jy, jz, ux, uy, uz, Fx, Fy, Fz);
     }
-    if (out.T) out.T[n] = (double)T;
-    if (out.fl) out.fl[n] = (double)fl;
+    if (out.T) out.T[n] = Td;
+    if (out.fl) out.fl[n] = fld;
     if (out.h) out.h[n] = h;
     if (out.rho) out.rho[n] = (double)rho;
     if (out.ux) out.ux[n] = (double)ux;
     if (out.uy) out.uy[n] = (double)uy;
     if (out.uz) out.uz[n] = (double)uz;
     if (acc) {
-        acc[0] += (double)fl;
+        acc[0] += fld;
         acc[1] += h;
         acc[2] += (double)rho;
         if (x == 0) {
             const double Tw = a.Tw[0][y + a.ny * z];
-            if (a.wall_iso[0]) acc[3] += 2.0 * ((double)g[1] + (double)k.gshift) - (double)k.wT_cref * Tw;
-            acc[4] += (Tw - (double)T) * 2.0;
+            if (a.wall_iso[0])
+                acc[3] += 2.0 * ((double)g[1] + (double)lo[1] + (double)k.gshift) -
+                          (double)k.wT_cref * Tw;
+            acc[4] += (Tw - Td) * 2.0;
         }
-        if (!isfinite(h) || !isfinite((double)rho)) acc[5] += 1.0;
+        const C gsum = ((g[1] + g[2]) + (g[3] + g[4])) + (g[5] + g[6]);
+        if (!isfinite(h) || !isfinite((double)rho) || !isfinite((double)gsum)) acc[5] += 1.0;
     }
     if (out.lines && y == a.ny / 2) {
-        if (z == a.nz / 4) out.lines[x] = (double)fl;
-        if (z == a.nz / 2) out.lines[a.nx + x] = (double)fl;
-        if (z == (3 * a.nz) / 4) out.lines[2 * a.nx + x] = (double)fl;
+        if (z == a.nz / 4) out.lines[x] = fld;
+        if (z == a.nz / 2) out.lines[a.nx + x] = fld;
+        if (z == (3 * a.nz) / 4) out.lines[2 * a.nx + x] = fld;
     }
 }
 
@@ -1080,7 +1269,7 @@ LBPC_HD double state_g(const Args& a, const Coef<C>& k, const double* Qg, const 
                        int q, int m) {
     if (Qg) return Qg[(size_t)q * a.N + m];
     C T, fl;
-    invert_excess(k, h0[m] - a.hs, T, fl);
+    invert_excess(a, h0[m] - a.hs, T, fl);
     return (double)(k.wa_cref * T);
 }
 
@@ -1112,19 +1301,30 @@ LBPC_HD void init_node(const Args& a, int x, int y, int z, const double* Qf, con
     }
 #define LBPC_IG(q, ex, ey, ez, op)                                                       \
     {                                                                                   \
+        using SG = Store<Mode<P>::G>;                                                   \
         double v;                                                                       \
-        if constexpr (LAYOUT == LAYOUT_AA_NATURAL) v = state_g(a, k, Qg, h0, q, n);     \
-        else {                                                                          \
-            const bool w = b.template wall<-(ex), -(ey), -(ez)>();                             \
+        int rface = -1; /* face whose residual this slot carries (16-bit g) */          \
+        if constexpr (LAYOUT == LAYOUT_AA_NATURAL) {                                    \
+            v = state_g(a, k, Qg, h0, q, n);                                            \
+            if (b.template wall<ex, ey, ez>() && a.wall_iso[q - 1]) rface = q - 1;      \
+        } else {                                                                        \
+            const bool w = b.template wall<-(ex), -(ey), -(ez)>();                      \
             if (w) {                                                                    \
                 v = state_g(a, k, Qg, h0, op, n);                                       \
-                if (a.wall_iso[op - 1])                                                 \
+                if (a.wall_iso[op - 1]) {                                               \
                     v = (double)k.wT_cref * a.Tw[op - 1][face_index(a, op - 1, x, y, z)] - v; \
+                    rface = op - 1;                                                     \
+                }                                                                       \
             } else {                                                                    \
-                v = state_g(a, k, Qg, h0, q, n + b.template off<-(ex), -(ey), -(ez)>());       \
+                v = state_g(a, k, Qg, h0, q, n + b.template off<-(ex), -(ey), -(ez)>()); \
             }                                                                           \
         }                                                                               \
-        gd[(size_t)(q - 1) * N + n] = Store<Mode<P>::G>::enc_g((C)(v - (double)k.gshift), C(0)); \
+        const C r = (C)(v - (double)k.gshift);                                          \
+        const auto st = SG::enc_g(r, C(0));                                             \
+        gd[(size_t)(q - 1) * N + n] = st;                                               \
+        if constexpr (SG::kGrid) {                                                      \
+            if (rface >= 0) a.wres[rface][face_index(a, rface, x, y, z)] = r - SG::dec(st, C(0)); \
+        }                                                                               \
     }
     LBPC_Q7(LBPC_IG)
 #undef LBPC_IG
@@ -1144,9 +1344,9 @@ LBPC_HD void init_hprime_node(const Args& a, int x, int y, int z, const double* 
     } else {
         h = h0[n];
     }
-    C g[7];
-    gather_g<Mode<P>::G, LAYOUT, true>(a, b, n, x, y, z, gs, g);
-    hp[n] = excess_minus<Mode<P>::G>(h - a.hs, g);
+    C g[7], lo[7] = {};
+    gather_g<Mode<P>::G, LAYOUT, true>(a, b, n, x, y, z, gs, g, lo);
+    hp[n] = add_lo<Mode<P>::G>(excess_minus<Mode<P>::G>(h - a.hs, g), lo, -1.0);
 }
 
 // Pre-collision populations of node (x, y, z) in FP64 (g_0 = h' = h_s + e').
@@ -1158,11 +1358,11 @@ LBPC_HD void dist_node(const Args& a, int x, int y, int z, const TF<P>* fs,
     const Nb b = make_nb(a, x, y, z);
     const size_t N = (size_t)a.N;
     const Coef<C>& k = coef<C>(a);
-    C g[7];
-    gather_g<Mode<P>::G, LAYOUT, true>(a, b, n, x, y, z, gs, g);
+    C g[7], lo[7] = {};
+    gather_g<Mode<P>::G, LAYOUT, true>(a, b, n, x, y, z, gs, g, lo);
     const double gs_ = (double)k.gshift;
     Qg[n] = a.hs + hp[n] - 6.0 * gs_;
-    for (int q = 1; q < 7; q++) Qg[(size_t)q * N + n] = (double)g[q] + gs_;
+    for (int q = 1; q < 7; q++) Qg[(size_t)q * N + n] = ((double)g[q] + (double)lo[q]) + gs_;
     if constexpr (FLOW) {
         if (Qf) {
             C f[19];
@@ -1385,11 +1585,11 @@ LBPC_HD CT<P> adj_seed_node(const Args& a, int x, int y, int z,
     const Coef<C>& k = coef<C>(a);
     const int n = x + a.nx * (y + a.ny * z);
     const Nb b = make_nb(a, x, y, z);
-    C g[7];
-    gather_g<Mode<P>::G, LAYOUT_PULL, true>(a, b, n, x, y, z, gs, g);
-    const double e = excess_plus<Mode<P>::G>(hp[n], g);
+    C g[7], lo[7] = {};
+    gather_g<Mode<P>::G, LAYOUT_PULL, true>(a, b, n, x, y, z, gs, g, lo);
+    const double e = add_lo<Mode<P>::G>(excess_plus<Mode<P>::G>(hp[n], g), lo, 1.0);
     C T, fl, dTde, dfde, dTdL, dfdL;
-    invert_excess_d(k, to_compute(e, C(0)), T, fl, dTde, dfde, dTdL, dfdL);
+    invert_excess_d(k, tape_excess(a, e, C(0)), T, fl, dTde, dfde, dTdL, dfdL);
     const size_t N = (size_t)a.N;
     const int nf = FLOW ? 19 : 0;
     for (int q = 0; q < nf; q++) lam[(size_t)q * N + n] = C(0);
@@ -1459,7 +1659,7 @@ LBPC_HD CT<P> adj_reverse_node(const Args& a, const NB& b, int x, int y, int z,
 // lambda_q of node x is lambda_{n+1} in plane q at x + e_q, or the reflected plane at x
 // when x + e_q lies behind an x wall; every other access is an aligned pair.
 template <int P, bool FLOW>
-LBPC_HD double adj_reverse_pair(const Args& a, int x0, int y, int z, const CT<P>* lin,
+LBPC_HD CT<P> adj_reverse_pair(const Args& a, int x0, int y, int z, const CT<P>* lin,
                                CT<P>* lout, const CT<P>* tape_e, const CT<P>* tape_m,
                                int wface, double* gtw) {
     using C = CT<P>;
@@ -1533,8 +1733,8 @@ LBPC_HD double adj_reverse_pair(const Args& a, int x0, int y, int z, const CT<P>
         jz0 = v.x; jz1 = v.y;
     }
     const VC d = ld_any<true>(reinterpret_cast<const VC*>(tape_e + n0));
-    const double dL = (double)collide_adjoint<C, FLOW>(k, d.x, r0, jx0, jy0, jz0, lf0, lg0) +
-                      (double)collide_adjoint<C, FLOW>(k, d.y, r1, jx1, jy1, jz1, lf1, lg1);
+    const C dL = collide_adjoint<C, FLOW>(k, d.x, r0, jx0, jy0, jz0, lf0, lg0) +
+                 collide_adjoint<C, FLOW>(k, d.y, r1, jx1, jy1, jz1, lf1, lg1);
     for (int q = 0; q < nf; q++)
         *reinterpret_cast<VC*>(lout + (size_t)q * N + n0) = VC{lf0[q], lf1[q]};
     for (int q = 0; q < 7; q++)
@@ -1551,6 +1751,11 @@ LBPC_HD double adj_reverse_pair(const Args& a, int x0, int y, int z, const CT<P>
     const int y = blockIdx.y * blockDim.y + threadIdx.y;                                \
     const int z = blockIdx.z;                                                           \
     if (x >= a.nx || y >= a.ny) return;
+
+// Whether the node pair (x0, x0 + 1) of a valid lane touches an isothermal x wall.
+__device__ __forceinline__ bool xwall_lane(const Args& a, int x0, bool valid) {
+    return valid && ((x0 == 0 && a.wall_iso[0]) || (x0 + 2 == a.nx && a.wall_iso[1]));
+}
 
 // One node per thread; with TAPE (pull) also the adjoint tape.
 template <int P, int KIND, int FLOW, bool TAPE>
@@ -1578,9 +1783,10 @@ k_step_pull_x2(const __grid_constant__ Args a, const TF<P>* fs,
     const bool valid = x0 < a.nx && y < a.ny;
     const bool inner = !valid || (y > 0 && y < a.ny - 1 && z > 0 && z < a.nz - 1);
     const bool paired = __all_sync(0xffffffffu, inner);
+    const bool xwall = Store<Mode<P>::G>::kGrid && __any_sync(0xffffffffu, xwall_lane(a, x0, valid));
     if (!valid) return;
     if (paired) {
-        step_pair_pull<P, FLOW, TAPE>(a, x0, y, z, fs, fd, gs, gd, hp, tape_e, tape_m);
+        step_pair_pull<P, FLOW, TAPE>(a, x0, y, z, fs, fd, gs, gd, hp, tape_e, tape_m, xwall);
     } else {
         step_node<P, STEP_PULL, FLOW, TAPE>(a, x0, y, z, fs, fd, gs, gd, hp, tape_e, tape_m);
         step_node<P, STEP_PULL, FLOW, TAPE>(a, x0 + 1, y, z, fs, fd, gs, gd, hp, tape_e, tape_m);
@@ -1599,10 +1805,11 @@ k_step_aa_x2(const __grid_constant__ Args a, TF<P>* F, TG<P>* G, double* __restr
     const bool valid = x0 < a.nx && y < a.ny;
     const bool inner = !valid || (y > 0 && y < a.ny - 1 && z > 0 && z < a.nz - 1);
     const bool paired = __all_sync(0xffffffffu, inner);
+    const bool xwall = Store<Mode<P>::G>::kGrid && __any_sync(0xffffffffu, xwall_lane(a, x0, valid));
     if (!valid) return;
     constexpr int KIND = ODD ? STEP_AA_ODD : STEP_AA_EVEN;
     if (paired) {
-        step_pair_aa<P, FLOW, ODD>(a, x0, y, z, F, G, hp);
+        step_pair_aa<P, FLOW, ODD>(a, x0, y, z, F, G, hp, xwall);
     } else {
         step_node<P, KIND, FLOW>(a, x0, y, z, F, F, G, G, hp);
         step_node<P, KIND, FLOW>(a, x0 + 1, y, z, F, F, G, G, hp);
@@ -1671,6 +1878,37 @@ k_dist(const __grid_constant__ Args a, const TF<P>* __restrict__ fs,
 }
 
 
+// Divergence check between steps: sets *flag when a stored g population (any of the six
+// planes, any layout) or the FP64 rest channel is not finite, by tests on the bits (all
+// exponent bits set).  A non-finite f reaches g within one step through u.
+template <class T> __device__ __forceinline__ bool nonfinite_bits(T v);
+template <> __device__ __forceinline__ bool nonfinite_bits<double>(double v) {
+    return ((__double_as_longlong(v) >> 52) & 0x7ff) == 0x7ff;
+}
+template <> __device__ __forceinline__ bool nonfinite_bits<float>(float v) {
+    return (__float_as_uint(v) & 0x7f800000u) == 0x7f800000u;
+}
+template <> __device__ __forceinline__ bool nonfinite_bits<__half>(__half v) {
+    return (__half_as_ushort(v) & 0x7c00u) == 0x7c00u;
+}
+template <> __device__ __forceinline__ bool nonfinite_bits<__nv_bfloat16>(__nv_bfloat16 v) {
+    return (__bfloat16_as_ushort(v) & 0x7f80u) == 0x7f80u;
+}
+template <int P>
+__global__ void __launch_bounds__(256)
+k_check(const __grid_constant__ Args a, const TG<P>* __restrict__ g,
+        const double* __restrict__ hp, int* flag) {
+    int bad = 0;
+    const size_t N = (size_t)a.N;
+    for (long long n = blockIdx.x * blockDim.x + threadIdx.x; n < a.N;
+         n += (long long)gridDim.x * blockDim.x) {
+        bad |= nonfinite_bits(hp[n]);
+#pragma unroll
+        for (int q = 0; q < 6; q++) bad |= nonfinite_bits(g[(size_t)q * N + n]);
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) *flag = 1;
+}
+
 // ---- adjoint kernels ----
 // Sum of v over the block (STEP_THREADS threads), valid in thread 0.
 __device__ __forceinline__ double block_sum(double v) {
@@ -1720,18 +1958,19 @@ k_adj_reverse(const __grid_constant__ Args a, const CT<P>* __restrict__ lin,
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
-    double dL = 0.0;
+    CT<P> dL = CT<P>(0);
     if (x < a.nx && y < a.ny) {
         if (is_interior(a, x, y, z))
-            dL = (double)adj_reverse_node<P, FLOW>(a, NbInterior{a.nx, a.nx * a.ny}, x, y, z, lin,
-                                                   lout, tape_e, tape_m, wface, gtw);
+            dL = adj_reverse_node<P, FLOW>(a, NbInterior{a.nx, a.nx * a.ny}, x, y, z, lin, lout,
+                                           tape_e, tape_m, wface, gtw);
         else
-            dL = (double)adj_reverse_node<P, FLOW>(a, make_nb(a, x, y, z), x, y, z, lin, lout,
-                                                   tape_e, tape_m, wface, gtw);
+            dL = adj_reverse_node<P, FLOW>(a, make_nb(a, x, y, z), x, y, z, lin, lout, tape_e,
+                                           tape_m, wface, gtw);
     }
-    // warp partials only: no block barrier in the reverse sweep
-    const double w = warp_sum(dL);
-    if (((threadIdx.x + blockDim.x * threadIdx.y) & 31) == 0) Lpart[warp_slot()] += w;
+    // warp partials only (no block barrier in the reverse sweep), summed within the warp in
+    // the compute precision and accumulated over warps and steps in FP64
+    const CT<P> w = warp_sum(dL);
+    if (((threadIdx.x + blockDim.x * threadIdx.y) & 31) == 0) Lpart[warp_slot()] += (double)w;
 }
 
 // Reverse step, two nodes per thread along x (even nx); the pull kernels' vote.
@@ -1747,19 +1986,19 @@ k_adj_reverse_x2(const __grid_constant__ Args a, const CT<P>* __restrict__ lin,
     const bool valid = x0 < a.nx && y < a.ny;
     const bool inner = !valid || (y > 0 && y < a.ny - 1 && z > 0 && z < a.nz - 1);
     const bool paired = __all_sync(0xffffffffu, inner);
-    double dL = 0.0;
+    CT<P> dL = CT<P>(0);
     if (valid) {
         if (paired) {
             dL = adj_reverse_pair<P, FLOW>(a, x0, y, z, lin, lout, tape_e, tape_m, wface, gtw);
         } else {
             for (int x = x0; x < x0 + 2; x++)
-                dL += (double)adj_reverse_node<P, FLOW>(a, make_nb(a, x, y, z), x, y, z, lin, lout,
-                                                        tape_e, tape_m, wface, gtw);
+                dL += adj_reverse_node<P, FLOW>(a, make_nb(a, x, y, z), x, y, z, lin, lout, tape_e,
+                                                tape_m, wface, gtw);
         }
     }
-    // warp partials only: no block barrier in the reverse sweep
-    const double w = warp_sum(dL);
-    if (((threadIdx.x + blockDim.x * threadIdx.y) & 31) == 0) Lpart[warp_slot()] += w;
+    // warp partials in the compute precision, accumulated in FP64 (see k_adj_reverse)
+    const CT<P> w = warp_sum(dL);
+    if (((threadIdx.x + blockDim.x * threadIdx.y) & 31) == 0) Lpart[warp_slot()] += (double)w;
 }
 
 // ---------------------------------------------------------------------------------
@@ -1912,9 +2151,15 @@ struct Impl {
                                                         (const C*)tape_m, wface, gtw, Lpart);
     }
 
+    static void check(const Args& a, const void* g, const double* hp, int* flag,
+                      cudaStream_t s) {
+        k_check<P><<<RED_BLOCKS, 256, 0, s>>>(a, (const TGp*)g, hp, flag);
+    }
+
     static const Launchers& table() {
         static const Launchers L = {&step, &macro, &init, &dist, &step_tape, &adj_seed,
-                                    &adj_reverse, sizeof(T), sizeof(TGp), sizeof(CT<P>)};
+                                    &adj_reverse, &check, sizeof(T), sizeof(TGp),
+                                    sizeof(CT<P>)};
         return L;
     }
 };

@@ -28,65 +28,7 @@ constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 double* g_scratch_addr[kMaxDevices] = {nullptr};
 
-// Same reduction as the workspace-backed diagnostics: fixed-order sums of the block
-// partials, then the LBPC_S_* scalars.
-__global__ void __launch_bounds__(256)
-k_finalize_noalloc(const double* __restrict__ partial, const double* __restrict__ lines, int nx,
-                   double area, double nu_scale, double fd_scale, double step, int flow, int iso0,
-                   double* __restrict__ result) {
-    __shared__ double sh[256][NRED];
-    double acc[NRED] = {0, 0, 0, 0, 0, 0};
-    for (int b = threadIdx.x; b < RED_BLOCKS; b += blockDim.x)
-        for (int k = 0; k < NRED; k++) acc[k] += partial[b * NRED + k];
-    for (int k = 0; k < NRED; k++) sh[threadIdx.x][k] = acc[k];
-    __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s)
-            for (int k = 0; k < NRED; k++) sh[threadIdx.x][k] += sh[threadIdx.x + s][k];
-        __syncthreads();
-    }
-    if (threadIdx.x != 0) return;
-    double front = 0.0;
-    for (int l = 0; l < 3; l++) {
-        const double* v = lines + (size_t)l * nx;
-        double xc = nx;
-        for (int x = 0; x < nx; x++) {
-            if (v[x] < 0.5) {
-                xc = x == 0 ? -0.5 : (x - 1) + (v[x - 1] - 0.5) / (v[x - 1] - v[x]);
-                break;
-            }
-        }
-        front += (xc + 0.5) / 3.0;
-    }
-    result[LBPC_S_LIQUID_VOL] = sh[0][0];
-    result[LBPC_S_NU_HOT] = iso0 ? nu_scale * sh[0][3] / area : 0.0;
-    result[LBPC_S_FRONT_MEAN] = sh[0][0] / area;
-    result[LBPC_S_SUM_H] = sh[0][1];
-    result[LBPC_S_SUM_RHO] = flow ? sh[0][2] : 0.0;
-    result[LBPC_S_STEP] = step;
-    result[LBPC_S_NU_FD] = fd_scale * sh[0][4] / area;
-    result[LBPC_S_FRONT_MID] = front;
-    result[LBPC_S_NAN] = sh[0][5];
-}
-
 }  // namespace
-
-// Handle internals used here (defined in lbpc_api.cu).
-namespace lbpc_noalloc_access {
-struct View {
-    const Launchers* L;
-    const Args* args;
-    Layout layout;
-    const void* f;
-    const void* g;
-    const double* hp;
-    int nx, ny, nz, device, flow, iso0;
-    double nu_scale, fd_scale, step;
-    cudaStream_t stream;
-};
-lbpc_status view(lbpc_handle* h, View* v);
-void set_error(lbpc_handle* h, const char* msg);
-}  // namespace lbpc_noalloc_access
 
 extern "C" lbpc_status lbpc_get_scalars_noalloc(lbpc_handle* h, double* out_dev) {
     using namespace lbpc_noalloc_access;
@@ -126,10 +68,11 @@ extern "C" lbpc_status lbpc_get_scalars_noalloc(lbpc_handle* h, double* out_dev)
     o.partial = scratch;
     o.lines = scratch + kPartials;
     v.L->macro(*v.args, v.layout, v.f, v.g, v.hp, o, v.stream);
-    k_finalize_noalloc<<<1, 256, 0, v.stream>>>(o.partial, o.lines, v.nx, (double)v.ny * v.nz,
-                                                v.nu_scale, v.fd_scale, v.step, v.flow, v.iso0,
-                                                out_dev);
-    const cudaError_t e = cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = finalize_reduction(o.partial, o.lines, v.nx, (double)v.ny * v.nz, v.nu_scale,
+                               v.fd_scale, v.step, v.flow, v.iso0, out_dev, nullptr, v.stream);
+    count_launches(h, 2);  // reduction pass + finalize
     if (e != cudaSuccess) {
         set_error(h, cudaGetErrorString(e));
         return LBPC_ERR_CUDA;

@@ -52,7 +52,7 @@ def test_param_block_layout_matches():
 ])
 def test_workspace_bytes_per_node(precision, streaming, flow, per_node):
     p = inp.Params(precision=precision, streaming=streaming, flow_model=flow, tau_g=0.8)
-    n = 64
+    n = 128
     ws = B.workspace_bytes((n, n, n), p)
     ws_half = B.workspace_bytes((n // 2, n // 2, n // 2), p)
     assert ws >= per_node * n ** 3

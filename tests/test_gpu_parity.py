@@ -362,14 +362,20 @@ def test_history_rows_and_host_fields():
         assert np.array_equal(Fd[k], Fh[k]), k
 
 
-def test_divergence_is_reported_and_blocks_stepping():
+@pytest.mark.parametrize("flow_model", [inp.FLOW_MRT, inp.FLOW_NONE])
+def test_divergence_is_reported_and_blocks_stepping(flow_model):
     shape = (8, 8, 8)
-    p = inp.Params(precision=inp.FP32, Ra=5e4, Pr=0.7, St=1.0, report_every=1)
+    p = inp.Params(flow_model=flow_model, precision=inp.FP32, Ra=5e4, Pr=0.7, St=1.0,
+                   tau_g=0.0 if flow_model else 0.9, report_every=1)
     g = LBPC(shape, p)
-    f, gq = inp.random_state(shape, seed=7)
-    f[3, 100] = np.nan  # a host-made bad state; no device fault involved
+    f, gq = inp.random_state(shape, seed=7, flow=flow_model != 0)
+    if flow_model:
+        f[3, 100] = np.nan  # a host-made bad state; no device fault involved
+    else:
+        gq[5, 100] = np.nan
     dev = torch.device("cuda")
-    g.set_distributions(torch.from_numpy(f).to(dev), torch.from_numpy(gq).to(dev))
+    g.set_distributions(torch.from_numpy(f).to(dev) if f is not None else None,
+                        torch.from_numpy(gq).to(dev))
     with pytest.raises(LbpcError) as e:
         g.step(2)
     assert e.value.status == B.LBPC_ERR_DIVERGED
@@ -378,6 +384,38 @@ def test_divergence_is_reported_and_blocks_stepping():
         g.step(1)
     assert e2.value.status == B.LBPC_ERR_STATE
     g.set_initial_h(np.zeros(512))
+    g.step(1)
+
+
+@pytest.mark.parametrize("streaming", [inp.PULL, inp.AA])
+@pytest.mark.parametrize("precision", [inp.FP32, inp.FP16])
+@pytest.mark.parametrize("flow_model", [inp.FLOW_MRT, inp.FLOW_NONE])
+def test_divergence_is_reported_without_diagnostics(streaming, precision, flow_model):
+    """report_every = 0: no diagnostics are recorded, and each stepping call checks the
+    FP64 rest channel once at its end.  A host-made non-finite population (of f, or of g
+    in a conduction-only run) reaches it within one step."""
+    shape = (10, 6, 5)
+    p = inp.Params(flow_model=flow_model, precision=precision, streaming=streaming, Ra=5e4,
+                   Pr=0.7, St=1.0, tau_g=0.0 if flow_model else 0.9, report_every=0)
+    g = LBPC(shape, p)
+    g.step(4)  # a finite state passes the check (AA: even, so a state can be loaded)
+    f, gq = inp.random_state(shape, seed=8, flow=flow_model != 0)
+    if flow_model:
+        f[7, 41] = np.inf
+    else:
+        gq[3, 41] = np.nan
+    dev = torch.device("cuda")
+    g.set_distributions(torch.from_numpy(f).to(dev) if f is not None else None,
+                        torch.from_numpy(gq).to(dev))
+    launches = g.launch_count
+    with pytest.raises(LbpcError) as e:
+        g.step(2)
+    assert e.value.status == B.LBPC_ERR_DIVERGED
+    assert g.launch_count == launches + 3  # two steps and one check
+    with pytest.raises(LbpcError) as e2:
+        g.step(1)
+    assert e2.value.status == B.LBPC_ERR_STATE
+    g.set_initial_h(np.zeros(int(np.prod(shape))))
     g.step(1)
 
 

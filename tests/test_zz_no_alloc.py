@@ -43,9 +43,11 @@ def test_noalloc_scalars_match_two_calls_in_a_row(streaming):
     for _ in range(2):  # two calls in a row on the same state
         assert _noalloc(lat, out) == B.LBPC_OK
         _check(out.cpu().numpy(), lat.scalars())
-    lat.step(30)  # and again after the state moved on
-    for _ in range(2):
+    lat.step(31)  # and again after the state moved on, at an even step count (AA: the
+    for _ in range(2):  # natural layout; above, after 51 steps, the swapped one)
+        launches = lat.launch_count
         assert _noalloc(lat, out) == B.LBPC_OK
+        assert lat.launch_count == launches + 2  # reduction pass and finalize
         _check(out.cpu().numpy(), lat.scalars())
 
 
