@@ -52,9 +52,9 @@ enum { LBPC_ENTH_MRT = 1, LBPC_ENTH_SRT = 2 };
  * f_l) inversion of Eq. 2 decides its branch on the FP64 excess h - h_s, exactly, in every
  * mode, and reports FP64 fields; the FP32 collision takes T and f_l formed in FP32 from
  * h - h_s rounded once to nearest.  FP16S / BF16S store f - w_a and g_a - (omega_T/2)
- * Cp_ref Tref in 16 bits (116 B per node update), the g populations crossing isothermal
- * faces kept to FP32 by a residual per boundary node; the _G32 modes store f that way and
- * g in FP32 (140 B), which keeps every enthalpy population at FP32 resolution. */
+ * Cp_ref Tref in 16 bits (116 B per node update); the _G32 modes store f that way and g in
+ * FP32 (140 B), which keeps the enthalpy populations and the wall fluxes they carry at
+ * FP32 resolution. */
 enum { LBPC_FP64 = 0, LBPC_FP32 = 1, LBPC_FP16S = 2, LBPC_BF16S = 3, LBPC_FP16S_G32 = 4,
        LBPC_BF16S_G32 = 5 };
 enum { LBPC_PULL = 0, LBPC_AA = 1 };
@@ -145,7 +145,7 @@ int lbpc_abi_version(void);
 /* Bytes of device workspace lbpc_create needs for this lattice and parameter block
  * (0 if the parameters are invalid).  Per node: 2 x (19 + 6) populations (pull) or
  * 1 x (19 + 6) (AA) in the storage precision, 8 B of h', 8 B of field staging; per face
- * node: 8 B of wall temperature, and 4 B of wall residual with 16-bit g.
+ * node: 8 B of wall temperature.
  * Passage: the state of the two lattices, D3Q19 (Eq. 48) and D3Q7 (Eq. 3); the sizing
  * itself has no counterpart in the paper.  No CUDA call. */
 size_t lbpc_workspace_bytes(int nx, int ny, int nz, const lbpc_params *p);
@@ -232,8 +232,7 @@ lbpc_status lbpc_set_distributions_dev(lbpc_handle *h, const double *f, const do
  * as lbpc_lattice_constants. */
 lbpc_status lbpc_get_lattice(const lbpc_handle *h, double *out, int n);
 
-/* Checkpoint of the full state (populations, h', wall fields, wall residuals, step) in
- * host memory:
+/* Checkpoint of the full state (populations, h', wall fields, step) in host memory:
  * lbpc_state_bytes() bytes; lbpc_load requires a handle of the same shape, precision
  * and streaming (LBPC_ERR_PARAM otherwise, or for a short buffer or a bad header).
  * Synchronous.  Passage: none (checkpoint/restart has no counterpart in the paper). */

@@ -22,7 +22,7 @@ namespace {
 
 // Byte offsets of every buffer inside the workspace.
 struct WsLayout {
-    size_t f[2], g[2], hp, tw[6], res[6], partial, lines, result, hist, stage, flag, total;
+    size_t f[2], g[2], hp, tw[6], partial, lines, result, hist, stage, flag, total;
 };
 
 constexpr size_t kAlign = 256;
@@ -37,10 +37,6 @@ size_t f_store_bytes(int precision) {
 size_t g_store_bytes(int precision) {
     return precision == LBPC_FP64 ? 8 : (precision == LBPC_FP16S || precision == LBPC_BF16S ? 2 : 4);
 }
-
-// 16-bit g storage keeps the g populations that cross isothermal faces to FP32 precision
-// (a residual array per face)
-bool wall_residuals(int precision) { return precision == LBPC_FP16S || precision == LBPC_BF16S; }
 
 long face_area(int nx, int ny, int nz, int face) {
     return face < 2 ? (long)ny * nz : (face < 4 ? (long)nx * nz : (long)nx * ny);
@@ -63,12 +59,6 @@ WsLayout ws_layout(int nx, int ny, int nz, const lbpc_params* p) {
     }
     w.hp = off; off = align_up(off + 8 * N);
     for (int f = 0; f < 6; f++) { w.tw[f] = off; off = align_up(off + 8 * face_area(nx, ny, nz, f)); }
-    // FP32 wall residuals of the g populations crossing each face (16-bit g storage only)
-    const bool res = wall_residuals(p->precision);
-    for (int f = 0; f < 6; f++) {
-        w.res[f] = off;
-        if (res) off = align_up(off + 4 * face_area(nx, ny, nz, f));
-    }
     w.partial = off; off = align_up(off + 8 * (size_t)RED_BLOCKS * NRED);
     w.lines = off; off = align_up(off + 8 * 3 * (size_t)nx);
     w.result = off; off = align_up(off + 8 * LBPC_S_COUNT);
@@ -169,7 +159,6 @@ struct lbpc_handle {
     WsLayout lay;
     void *f[2], *g[2];
     double *hp, *tw[6], *partial, *lines, *result, *hist, *stage;
-    float* wres[6];  // wall residual arrays (null without 16-bit g)
     int* flag;
     int cur;
     long long step;
@@ -181,7 +170,7 @@ struct lbpc_handle {
         char* ws = nullptr;
         int nsteps = 0, k = 0, nseg = 0;
         long long end_step = 0;
-        size_t ckpt_bytes = 0, off_f = 0, off_g = 0, off_hp = 0, off_res = 0;
+        size_t ckpt_bytes = 0, off_f = 0, off_g = 0, off_hp = 0;
         char* ckpt = nullptr;
         void* tape_e = nullptr;
         void* tape_m = nullptr;
@@ -335,8 +324,6 @@ lbpc_status lbpc_create(int nx, int ny, int nz, const lbpc_params* p, void* dev_
     if (p->streaming == LBPC_AA) { h->f[1] = h->f[0]; h->g[1] = h->g[0]; }
     h->hp = (double*)(h->ws + lay.hp);
     for (int f = 0; f < 6; f++) h->tw[f] = (double*)(h->ws + lay.tw[f]);
-    for (int f = 0; f < 6; f++)
-        h->wres[f] = wall_residuals(p->precision) ? (float*)(h->ws + lay.res[f]) : nullptr;
     h->partial = (double*)(h->ws + lay.partial);
     h->lines = (double*)(h->ws + lay.lines);
     h->result = (double*)(h->ws + lay.result);
@@ -344,7 +331,7 @@ lbpc_status lbpc_create(int nx, int ny, int nz, const lbpc_params* p, void* dev_
     h->stage = (double*)(h->ws + lay.stage);
     h->flag = (int*)(h->ws + lay.flag);
 
-    fill_args(h->args, nx, ny, nz, *p, d, h->tw, h->wres);
+    fill_args(h->args, nx, ny, nz, *p, d, h->tw);
 
     lbpc_status s = set_device(h);
     if (s == LBPC_OK) {
@@ -570,21 +557,13 @@ struct StateHeader {
     int64_t step;
 };
 
-// bytes of the wall residual arrays (all six faces; 0 without 16-bit g)
-size_t res_bytes(const lbpc_handle* h) {
-    if (!h->wres[0]) return 0;
-    size_t b = 0;
-    for (int f = 0; f < 6; f++) b += 4 * face_area(h->nx, h->ny, h->nz, f);
-    return b;
-}
-
 size_t state_pop_bytes(const lbpc_handle* h, size_t* fb, size_t* gb) {
     const size_t N = (size_t)h->N;
     *fb = h->p.flow_model != LBPC_FLOW_NONE ? 19 * N * h->L->f_bytes : 0;
     *gb = 6 * N * h->L->g_bytes;
     size_t tw = 0;
     for (int f = 0; f < 6; f++) tw += 8 * face_area(h->nx, h->ny, h->nz, f);
-    return sizeof(StateHeader) + *fb + *gb + 8 * N + tw + res_bytes(h);
+    return sizeof(StateHeader) + *fb + *gb + 8 * N + tw;
 }
 }  // namespace
 
@@ -601,7 +580,7 @@ lbpc_status lbpc_save(lbpc_handle* h, void* host_buf, size_t bytes) {
     if (!host_buf || bytes < need) return fail(h, LBPC_ERR_PARAM, "buffer smaller than lbpc_state_bytes()");
     lbpc_status s = set_device(h);
     if (s != LBPC_OK) return s;
-    StateHeader hd{kStateMagic, 2, h->nx, h->ny, h->nz, h->p.precision, h->p.streaming,
+    StateHeader hd{kStateMagic, 1, h->nx, h->ny, h->nz, h->p.precision, h->p.streaming,
                    h->p.flow_model != LBPC_FLOW_NONE, h->step};
     char* o = (char*)host_buf;
     std::memcpy(o, &hd, sizeof hd);
@@ -615,11 +594,6 @@ lbpc_status lbpc_save(lbpc_handle* h, void* host_buf, size_t bytes) {
         LBPC_CK(h, cudaMemcpy(o, h->tw[f], b, cudaMemcpyDeviceToHost));
         o += b;
     }
-    for (int f = 0; f < 6 && h->wres[0]; f++) {
-        const size_t b = 4 * face_area(h->nx, h->ny, h->nz, f);
-        LBPC_CK(h, cudaMemcpy(o, h->wres[f], b, cudaMemcpyDeviceToHost));
-        o += b;
-    }
     return LBPC_OK;
 }
 
@@ -630,7 +604,7 @@ lbpc_status lbpc_load(lbpc_handle* h, const void* host_buf, size_t bytes) {
     if (!host_buf || bytes < need) return fail(h, LBPC_ERR_PARAM, "buffer smaller than lbpc_state_bytes()");
     StateHeader hd;
     std::memcpy(&hd, host_buf, sizeof hd);
-    if (hd.magic != kStateMagic || hd.version != 2 || hd.nx != h->nx || hd.ny != h->ny ||
+    if (hd.magic != kStateMagic || hd.version != 1 || hd.nx != h->nx || hd.ny != h->ny ||
         hd.nz != h->nz || hd.precision != h->p.precision || hd.streaming != h->p.streaming ||
         hd.flow != (h->p.flow_model != LBPC_FLOW_NONE))
         return fail(h, LBPC_ERR_PARAM, "checkpoint does not match this handle");
@@ -644,11 +618,6 @@ lbpc_status lbpc_load(lbpc_handle* h, const void* host_buf, size_t bytes) {
     for (int f = 0; f < 6; f++) {
         const size_t b = 8 * face_area(h->nx, h->ny, h->nz, f);
         LBPC_CK(h, cudaMemcpy(h->tw[f], o, b, cudaMemcpyHostToDevice));
-        o += b;
-    }
-    for (int f = 0; f < 6 && h->wres[0]; f++) {
-        const size_t b = 4 * face_area(h->nx, h->ny, h->nz, f);
-        LBPC_CK(h, cudaMemcpy(h->wres[f], o, b, cudaMemcpyHostToDevice));
         o += b;
     }
     h->step = hd.step;
@@ -679,7 +648,7 @@ void lbpc_destroy(lbpc_handle* h) {
 namespace {
 
 struct AdjLayout {
-    size_t ckpt_bytes, off_f, off_g, off_hp, off_res, ckpt, tape_e, tape_m, lam0, lam1, gtw, Lpart, Jpart,
+    size_t ckpt_bytes, off_f, off_g, off_hp, ckpt, tape_e, tape_m, lam0, lam1, gtw, Lpart, Jpart,
         red, total;
     int nseg, nblocks;
 };
@@ -693,8 +662,7 @@ AdjLayout adj_layout(const lbpc_handle* h, int nsteps, int k) {
     L.off_f = 0;
     L.off_g = align_up(flow ? 19 * N * Sf : 0);
     L.off_hp = L.off_g + align_up(6 * N * Sg);
-    L.off_res = L.off_hp + align_up(8 * N);  // wall residuals (16-bit g), all faces
-    L.ckpt_bytes = L.off_res + align_up(res_bytes(h));
+    L.ckpt_bytes = L.off_hp + align_up(8 * N);
     size_t off = 0;
     // slots 0 .. nseg - 2: segment starts; slot nseg - 1: spare for the recompute
     L.ckpt = off; off += (size_t)(L.nseg > 1 ? L.nseg : 0) * L.ckpt_bytes;
@@ -714,32 +682,6 @@ AdjLayout adj_layout(const lbpc_handle* h, int nsteps, int k) {
     return L;
 }
 
-// The wall residual arrays (16-bit g) to (to_slot) or from a checkpoint slot's copy.
-lbpc_status copy_residuals(lbpc_handle* h, char* slot_res, bool to_slot) {
-    size_t off = 0;
-    for (int f = 0; f < 6 && h->wres[0]; f++) {
-        const size_t b = 4 * face_area(h->nx, h->ny, h->nz, f);
-        void* dst = to_slot ? (void*)(slot_res + off) : (void*)h->wres[f];
-        const void* src = to_slot ? (const void*)h->wres[f] : (const void*)(slot_res + off);
-        LBPC_CK(h, cudaMemcpyAsync(dst, src, b, cudaMemcpyDeviceToDevice, h->stream));
-        off += b;
-    }
-    return LBPC_OK;
-}
-
-// Kernel arguments whose wall residual arrays are a checkpoint slot's copy.
-Args args_on_slot(const lbpc_handle* h, char* slot_res) {
-    Args a = h->args;
-    size_t off = 0;
-    for (int f = 0; f < 6; f++) {
-        if (h->wres[0]) {
-            a.wres[f] = a.wall_iso[f] ? (float*)(slot_res + off) : nullptr;
-            off += 4 * face_area(h->nx, h->ny, h->nz, f);
-        }
-    }
-    return a;
-}
-
 lbpc_status save_state(lbpc_handle* h, char* dst) {
     auto& A = h->adj;
     const size_t N = (size_t)h->N, Sf = h->L->f_bytes, Sg = h->L->g_bytes;
@@ -747,7 +689,7 @@ lbpc_status save_state(lbpc_handle* h, char* dst) {
         LBPC_CK(h, cudaMemcpyAsync(dst + A.off_f, h->f[h->cur], 19 * N * Sf, cudaMemcpyDeviceToDevice, h->stream));
     LBPC_CK(h, cudaMemcpyAsync(dst + A.off_g, h->g[h->cur], 6 * N * Sg, cudaMemcpyDeviceToDevice, h->stream));
     LBPC_CK(h, cudaMemcpyAsync(dst + A.off_hp, h->hp, 8 * N, cudaMemcpyDeviceToDevice, h->stream));
-    return copy_residuals(h, dst + A.off_res, true);
+    return LBPC_OK;
 }
 
 }  // namespace
@@ -781,7 +723,7 @@ lbpc_status lbpc_adjoint_forward(lbpc_handle* h, int nsteps, int ckpt_every, voi
     A.nseg = L.nseg;
     A.nblocks = L.nblocks;
     A.ckpt_bytes = L.ckpt_bytes;
-    A.off_f = L.off_f; A.off_g = L.off_g; A.off_hp = L.off_hp; A.off_res = L.off_res;
+    A.off_f = L.off_f; A.off_g = L.off_g; A.off_hp = L.off_hp;
     A.ckpt = w + L.ckpt;
     A.tape_e = w + L.tape_e;
     A.tape_m = w + L.tape_m;
@@ -818,8 +760,6 @@ lbpc_status lbpc_adjoint_forward(lbpc_handle* h, int nsteps, int ckpt_every, voi
             if (to_ckpt) {
                 LBPC_CK(h, cudaMemcpyAsync(slot + A.off_hp, h->hp, 8 * (size_t)h->N,
                                            cudaMemcpyDeviceToDevice, h->stream));
-                s = copy_residuals(h, slot + A.off_res, true);
-                if (s != LBPC_OK) return s;
             } else {
                 h->cur = nb;
             }
@@ -871,11 +811,10 @@ lbpc_status lbpc_adjoint_backward(lbpc_handle* h, int face, double* dJ_dTw_host,
                            A.ckpt + (size_t)(seg + 1) * A.ckpt_bytes};
             const bool flow = h->p.flow_model != LBPC_FLOW_NONE;
             double* hp = (double*)(ck[0] + A.off_hp);
-            const Args ra = args_on_slot(h, ck[0] + A.off_res);  // residuals in place, too
             for (int t = 0; t < len; t++) {
                 char* src = ck[t & 1];
                 char* dst = ck[(t + 1) & 1];
-                h->L->step_tape(ra, flow ? src + A.off_f : nullptr,
+                h->L->step_tape(h->args, flow ? src + A.off_f : nullptr,
                                 flow ? dst + A.off_f : nullptr, src + A.off_g, dst + A.off_g, hp,
                                 (char*)A.tape_e + (size_t)t * N * Cb,
                                 (char*)A.tape_m + (size_t)t * 4 * N * Cb, h->stream);

@@ -184,10 +184,9 @@ inline void fill_coef(Coef<C>& c, const lbpc_params& p, const Derived& d) {
 }
 
 // Kernel argument block of a validated parameter block; Tw[f] are the device (or host,
-// for host-side evaluation) wall temperature fields of the six faces, wres[f] the wall
-// residual arrays (used for isothermal faces with 16-bit g; may be null otherwise).
+// for host-side evaluation) wall temperature fields of the six faces.
 inline void fill_args(Args& a, int nx, int ny, int nz, const lbpc_params& p, const Derived& d,
-                      double* const Tw[6], float* const wres[6]) {
+                      double* const Tw[6]) {
     std::memset(&a, 0, sizeof a);
     a.nx = nx; a.ny = ny; a.nz = nz; a.N = nx * ny * nz;
     for (int ax = 0; ax < 3; ax++) a.per[ax] = p.bc[2 * ax] == LBPC_PERIODIC;
@@ -195,7 +194,6 @@ inline void fill_args(Args& a, int nx, int ny, int nz, const lbpc_params& p, con
         a.wall[f] = p.bc[f] != LBPC_PERIODIC;
         a.wall_iso[f] = p.bc[f] == LBPC_ISOTHERMAL;
         a.Tw[f] = Tw[f];
-        a.wres[f] = a.wall_iso[f] ? wres[f] : nullptr;
     }
     a.flow = p.flow_model != LBPC_FLOW_NONE;
     a.hs = d.hs;

@@ -44,8 +44,6 @@ struct Args {
     int wall_iso[6];     // face is an isothermal wall (anti-bounce-back of g)
     int wall[6];         // face is a wall (not periodic)
     const double* Tw[6]; // per-face wall temperature fields (device)
-    float* wres[6];      // per-face FP32 residuals of the wall g populations (16-bit g and
-                         // isothermal faces only; else null)
     int flow;            // flow lattice present
     double hs, L;        // FP64 copies for the enthalpy inversion
     long long Lbits;     // bits of L as a signed integer (branch tests of the inversion)

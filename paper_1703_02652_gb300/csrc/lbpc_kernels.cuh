@@ -322,18 +322,10 @@ LBPC_HD void gather_f(const Args& a, const NB& b, int n,
 
 // g_1..6 (g[0] is not gathered: the rest population is the FP64 channel h').  The g
 // lattice holds six planes: population q lives in plane q - 1.
-//
-// Wall residuals (16-bit g): a population that crosses an isothermal face is kept to FP32
-// precision, as its 16-bit stored value plus the FP32 residual in a per-face array wres[f]
-// (one value per boundary node): the outgoing post-collision population in the pull and
-// the swapped AA layout, the incoming pre-collision one in the natural AA layout.  The
-// anti-bounce-back value -(g*_out + rho) + omega_T Cp_ref T_w is returned split into a
-// part on the 2^-20 grid (g[q]) and an FP32 remainder (lo[q]), so that e = e' + sum g +
-// sum lo stays exact; the wall flux then carries no 16-bit rounding.  lo must start at 0.
 template <int P, int LAYOUT, bool NC, class NB>
 LBPC_HD void gather_g(const Args& a, const NB& b, int n, int x, int y, int z,
-                      const typename Store<P>::T* gs, typename Store<P>::C* g,
-                      typename Store<P>::C* lo) {
+                                         const typename Store<P>::T* gs,
+                                         typename Store<P>::C* g) {
     using S = Store<P>;
     using C = typename S::C;
     const Coef<C>& k = coef<C>(a);
@@ -341,28 +333,15 @@ LBPC_HD void gather_g(const Args& a, const NB& b, int n, int x, int y, int z,
 #define LBPC_GG(q, ex, ey, ez, op)                                                       \
     {                                                                                   \
         if constexpr (LAYOUT == LAYOUT_AA_NATURAL) {                                    \
-            g[q] = S::dec(ldv<P, LAYOUT, NC>(gs + (size_t)(q - 1) * N + n), k.gshift);  \
-            if constexpr (S::kGrid) {                                                   \
-                if (b.template wall<ex, ey, ez>() && a.wall_iso[q - 1])                  \
-                    lo[q] = a.wres[q - 1][face_index(a, q - 1, x, y, z)];               \
-            }                                                                           \
+            g[q] = S::dec(ldv<P, LAYOUT, NC>(gs + (size_t)(q - 1) * N + n), k.gshift);         \
         } else {                                                                        \
-            const bool w = b.template wall<ex, ey, ez>();                               \
-            const int idx = w ? n : n + b.template off<ex, ey, ez>();                   \
+            const bool w = b.template wall<ex, ey, ez>();                                      \
+            const int idx = w ? n : n + b.template off<ex, ey, ez>();                          \
             int slot;                                                                   \
-            if constexpr (LAYOUT == LAYOUT_PULL) slot = w ? op : q;                     \
+            if constexpr (LAYOUT == LAYOUT_PULL) slot = w ? op : q;                      \
             else slot = w ? q : op;                                                     \
-            C v = S::dec(ldv<P, LAYOUT, NC>(gs + (size_t)(slot - 1) * N + idx), k.gshift); \
-            if (w && a.wall_iso[q - 1]) {                                               \
-                const C src = abb_source(a, k, q - 1, x, y, z);                         \
-                if constexpr (S::kGrid) {                                               \
-                    const C hi = S::grid(src);                                          \
-                    lo[q] = (src - hi) - a.wres[q - 1][face_index(a, q - 1, x, y, z)];  \
-                    v = hi - v;                                                         \
-                } else {                                                                \
-                    v = S::grid(src - v);                                               \
-                }                                                                       \
-            }                                                                           \
+            C v = S::dec(ldv<P, LAYOUT, NC>(gs + (size_t)(slot - 1) * N + idx), k.gshift);     \
+            if (w && a.wall_iso[q - 1]) v = S::grid(-v + abb_source(a, k, q - 1, x, y, z)); \
             g[q] = v;                                                                   \
         }                                                                               \
     }
@@ -399,113 +378,37 @@ LBPC_HD void scatter_f(const Args& a, const NB& b, int n,
 }
 
 // Stores g*_1..6 and replaces g[a] by the value as stored (rounded to the storage
-// precision), which is what the downwind neighbours will read.  16-bit g: a population
-// leaving through an isothermal face also leaves its residual (g* minus the stored value)
-// in wres and in lo[q], which the rest channel accounts for; in the odd AA step the
-// incoming anti-bounce-back value is formed from the unrounded g* and its own residual
-// kept.  lo must start at 0.
+// precision), which is what the downwind neighbours will read.
 template <int P, int KIND, class NB>
 LBPC_HD void scatter_g(const Args& a, const NB& b, int n, int x, int y, int z,
-                       typename Store<P>::T* gd, typename Store<P>::C* g,
-                       typename Store<P>::C* lo) {
+                       typename Store<P>::T* gd, typename Store<P>::C* g) {
     using S = Store<P>;
     using C = typename S::C;
     const Coef<C>& k = coef<C>(a);
     const size_t N = (size_t)a.N;
 #define LBPC_SG(q, ex, ey, ez, op)                                                       \
     {                                                                                   \
-        const C val = g[q];                                                             \
-        const auto v = S::enc_g(val, k.gshift);                                         \
+        const auto v = S::enc_g(g[q], k.gshift);                                        \
         g[q] = S::dec(v, k.gshift);                                                     \
-        const bool w = b.template wall<-(ex), -(ey), -(ez)>();                          \
-        const bool iso = w && a.wall_iso[op - 1];                                       \
-        if constexpr (S::kGrid) {                                                       \
-            if (iso) lo[q] = val - g[q];                                                \
-        }                                                                               \
-        if constexpr (KIND == STEP_PULL || KIND == STEP_AA_EVEN) {                      \
-            gd[(size_t)((KIND == STEP_PULL ? q : op) - 1) * N + n] = v;                 \
-            if constexpr (S::kGrid) {                                                   \
-                if (iso) a.wres[op - 1][face_index(a, op - 1, x, y, z)] = lo[q];        \
-            }                                                                           \
+        if constexpr (KIND == STEP_PULL) {                                              \
+            gd[(size_t)(q - 1) * N + n] = v;                                                  \
+        } else if constexpr (KIND == STEP_AA_EVEN) {                                    \
+            gd[(size_t)(op - 1) * N + n] = v;                                                 \
         } else {                                                                        \
+            const bool w = b.template wall<-(ex), -(ey), -(ez)>();                             \
             if (w) {                                                                    \
                 auto vb = v;                                                            \
-                if (iso) {                                                              \
-                    const C src = abb_source(a, k, op - 1, x, y, z);                    \
-                    if constexpr (S::kGrid) {                                           \
-                        const C in = src - val;                                         \
-                        vb = S::enc_g(in, k.gshift);                                    \
-                        a.wres[op - 1][face_index(a, op - 1, x, y, z)] =                \
-                            in - S::dec(vb, k.gshift);                                  \
-                    } else {                                                            \
-                        vb = S::enc_g(src - g[q], k.gshift);                            \
-                    }                                                                   \
-                }                                                                       \
-                gd[(size_t)(op - 1) * N + n] = vb;                                      \
+                if (a.wall_iso[op - 1])                                                 \
+                    vb = S::enc_g(-S::dec(v, k.gshift) + abb_source(a, k, op - 1, x, y, z), \
+                                  k.gshift);                                            \
+                gd[(size_t)(op - 1) * N + n] = vb;                                            \
             } else {                                                                    \
-                gd[(size_t)(q - 1) * N + n + b.template off<-(ex), -(ey), -(ez)>()] = v; \
+                gd[(size_t)(q - 1) * N + n + b.template off<-(ex), -(ey), -(ez)>()] = v;             \
             }                                                                           \
         }                                                                               \
     }
     LBPC_Q7(LBPC_SG)
 #undef LBPC_SG
-}
-
-// Anti-bounce-back value of the g population entering through isothermal face `face` at
-// a boundary node, from the stored outgoing value v (representation): 32-bit g gives it
-// directly; 16-bit g adds the outgoing residual and splits the result into the grid part
-// (returned) and the remainder (lo), as gather_g does.
-template <int PG>
-LBPC_HD float wall_in(const Args& a, const Coef<float>& k, int face, int x, int y, int z,
-                      float v, float& lo) {
-    using S = Store<PG>;
-    const float src = abb_source(a, k, face, x, y, z);
-    if constexpr (S::kGrid) {
-        const float hi = S::grid(src);
-        lo = (src - hi) - a.wres[face][face_index(a, face, x, y, z)];
-        return hi - v;
-    } else {
-        return S::grid(src - v);
-    }
-}
-// 16-bit g: residual of a population leaving through x face `face` (its post-collision
-// value minus the value stored), written to the face's residual array; returns it as
-// the FP64 amount the rest channel gives up besides the stored value.
-template <int PG>
-LBPC_HD double wall_out(const Args& a, int face, int y, int z, float val, float stored) {
-    const float r = val - stored;
-    a.wres[face][y + a.ny * z] = r;
-    return f2d_exact(r);
-}
-
-// Odd AA step: the stored anti-bounce-back value that enters through isothermal x face
-// `face` for the next (even) step, from the unrounded outgoing population out (v: its
-// stored value, the rounded form used by 32-bit g); 16-bit g keeps its residual in wres.
-template <int PG>
-LBPC_HD typename Store<PG>::T wall_in_aa(const Args& a, const Coef<float>& k, int face, int x,
-                                         int y, int z, float out, typename Store<PG>::T v) {
-    using S = Store<PG>;
-    const float src = abb_source(a, k, face, x, y, z);
-    if constexpr (S::kGrid) {
-        const float in = src - out;
-        const auto vb = S::enc_g(in, k.gshift);
-        a.wres[face][y + a.ny * z] = in - S::dec(vb, k.gshift);
-        return vb;
-    } else {
-        return S::enc_g(src - S::dec(v, k.gshift), k.gshift);
-    }
-}
-
-// Sum of the FP32 wall remainders lo[1..6] added to (sign +1) or taken from (-1) an FP64
-// value, one exact FP64 addition per nonzero remainder.
-template <int P>
-LBPC_HD double add_lo(double v, const typename Store<P>::C* lo, double sign) {
-    if constexpr (Store<P>::kGrid) {
-#pragma unroll
-        for (int q = 1; q < 7; q++)
-            if (lo[q] != 0.0f) v += sign * f2d_exact(lo[q]);
-    }
-    return v;
 }
 
 // ---------------------------------------------------------------------------------
@@ -833,22 +736,15 @@ LBPC_HD void step_node(const Args& a, int x, int y, int z, const TF<P>* fs,
     const NbInterior bi{a.nx, a.nx * a.ny};
     const Nb b = make_nb(a, x, y, z);
 
-    C f[19], g[7], lo[7] = {};
+    C f[19], g[7];
     if (interior) {
         if constexpr (FLOW) gather_f<Mode<P>::F, LAYOUT, NC>(a, bi, n, fs, f);
-        gather_g<Mode<P>::G, LAYOUT, NC>(a, bi, n, x, y, z, gs, g, lo);
+        gather_g<Mode<P>::G, LAYOUT, NC>(a, bi, n, x, y, z, gs, g);
     } else {
         if constexpr (FLOW) gather_f<Mode<P>::F, LAYOUT, NC>(a, b, n, fs, f);
-        gather_g<Mode<P>::G, LAYOUT, NC>(a, b, n, x, y, z, gs, g, lo);
+        gather_g<Mode<P>::G, LAYOUT, NC>(a, b, n, x, y, z, gs, g);
     }
-    // h - h_s; with wall remainders (16-bit g) the collision sees the full FP32 values
-    const double e = add_lo<Mode<P>::G>(excess_plus<Mode<P>::G>(hp[n], g), lo, 1.0);
-    if constexpr (Store<Mode<P>::G>::kGrid) {
-        for (int q = 1; q < 7; q++) {
-            g[q] += lo[q];
-            lo[q] = C(0);
-        }
-    }
+    const double e = excess_plus<Mode<P>::G>(hp[n], g);  // h - h_s
 
     C T, fl;
     invert_excess(a, e, T, fl);
@@ -867,12 +763,12 @@ LBPC_HD void step_node(const Args& a, int x, int y, int z, const TF<P>* fs,
     collide_enth<C, !FLOW>(g, k, T, fl, ux, uy, uz);
     if (interior) {
         if constexpr (FLOW) scatter_f<Mode<P>::F, KIND>(a, bi, n, fd, f);
-        scatter_g<Mode<P>::G, KIND>(a, bi, n, x, y, z, gd, g, lo);
+        scatter_g<Mode<P>::G, KIND>(a, bi, n, x, y, z, gd, g);
     } else {
         if constexpr (FLOW) scatter_f<Mode<P>::F, KIND>(a, b, n, fd, f);
-        scatter_g<Mode<P>::G, KIND>(a, b, n, x, y, z, gd, g, lo);
+        scatter_g<Mode<P>::G, KIND>(a, b, n, x, y, z, gd, g);
     }
-    hp[n] = add_lo<Mode<P>::G>(excess_minus<Mode<P>::G>(e, g), lo, -1.0);
+    hp[n] = excess_minus<Mode<P>::G>(e, g);
 }
 
 
@@ -914,13 +810,11 @@ LBPC_HD void pair_collide(const Args& a, CT<P>* f0, CT<P>* f1, CT<P>* g0, CT<P>*
 // rules (periodic wrap; at a wall the reflected population of the node itself) applied
 // by selecting a 32-bit element offset from the population's plane on the lanes at x = 0
 // / x = nx - 1; every store is a pair.  Requires even nx.
-// xwall (16-bit g): some lane of the warp owns a node on an isothermal x wall; the wall
-// work of the other warps is then skipped by a warp-uniform branch.
 template <int P, int FLOW, bool TAPE = false>
 LBPC_HD void step_pair_pull(const Args& a, int x0, int y, int z, const TF<P>* fs,
                             TF<P>* fd, const TG<P>* gs,
                             TG<P>* gd, double* hp, CT<P>* tape_e = nullptr,
-                            CT<P>* tape_m = nullptr, bool xwall = false) {
+                            CT<P>* tape_m = nullptr) {
     using SF = Store<Mode<P>::F>;
     using SG = Store<Mode<P>::G>;
     using TFt = typename SF::T;
@@ -937,9 +831,6 @@ LBPC_HD void step_pair_pull(const Args& a, int x0, int y, int z, const TF<P>* fs
     const int n0 = x0 + a.nx * (y + a.ny * z), n1 = n0 + 1;
     const bool xlo = x0 == 0, xhi = x0 + 1 == a.nx - 1;
     const bool wlo = xlo && a.wall[0], whi = xhi && a.wall[1];
-    const bool iso0 = wlo && a.wall_iso[0], iso1 = whi && a.wall_iso[1];
-    const bool wwarp = !SG::kGrid || xwall;  // 16-bit g: wall work only in wall warps
-    C lo0 = C(0), lo1 = C(0);  // wall remainders of the incoming g (16-bit g)
     // upwind x-neighbour of node 0 for e_x = +1 and of node 1 for e_x = -1 (with wrap)
     const int up0 = xlo ? n0 + a.nx - 1 : n0 - 1;
     const int up1 = xhi ? n1 - (a.nx - 1) : n1 + 1;
@@ -976,13 +867,13 @@ LBPC_HD void step_pair_pull(const Args& a, int x0, int y, int z, const TF<P>* fs
         } else if constexpr ((ex) == 1) {                                               \
             const int i0 = wlo ? ((op) - (q)) * N32 + n0 : up0 + oyz;                   \
             C v = SG::dec(ldv<Mode<P>::G, LAYOUT_PULL, true>(pl + i0), k.gshift);                 \
-            if (wwarp && iso0) v = wall_in<Mode<P>::G>(a, k, 0, x0, y, z, v, lo0);      \
+            if (wlo && a.wall_iso[0]) v = SG::grid(-v + abb_source(a, k, 0, x0, y, z)); \
             g0[q] = v;                                                                  \
             g1[q] = SG::dec(ldv<Mode<P>::G, LAYOUT_PULL, true>(pl + n0 + oyz), k.gshift);         \
         } else {                                                                        \
             const int i1 = whi ? ((op) - (q)) * N32 + n1 : up1 + oyz;                   \
             C v = SG::dec(ldv<Mode<P>::G, LAYOUT_PULL, true>(pl + i1), k.gshift);                 \
-            if (wwarp && iso1) v = wall_in<Mode<P>::G>(a, k, 1, x0 + 1, y, z, v, lo1);  \
+            if (whi && a.wall_iso[1]) v = SG::grid(-v + abb_source(a, k, 1, x0 + 1, y, z)); \
             g1[q] = v;                                                                  \
             g0[q] = SG::dec(ldv<Mode<P>::G, LAYOUT_PULL, true>(pl + n1 + oyz), k.gshift);         \
         }                                                                               \
@@ -990,15 +881,8 @@ LBPC_HD void step_pair_pull(const Args& a, int x0, int y, int z, const TF<P>* fs
     LBPC_Q7(LBPC_PG)
 #undef LBPC_PG
     const double2 ep = ld_any<true>(reinterpret_cast<const double2*>(hp + n0));
-    double e0 = excess_plus<Mode<P>::G>(ep.x, g0), e1 = excess_plus<Mode<P>::G>(ep.y, g1);
-    if constexpr (SG::kGrid) {  // the wall remainders (16-bit g): exact FP64 additions
-        if (xwall) {
-            if (iso0) { e0 += f2d_exact(lo0); g0[1] += lo0; }
-            if (iso1) { e1 += f2d_exact(lo1); g1[2] += lo1; }
-        }
-    }
+    const double e0 = excess_plus<Mode<P>::G>(ep.x, g0), e1 = excess_plus<Mode<P>::G>(ep.y, g1);
     pair_collide<P, FLOW, TAPE>(a, f0, f1, g0, g1, e0, e1, n0, tape_e, tape_m);
-    const C out0 = g0[2], out1 = g1[1];  // populations leaving through the x walls
     if constexpr (FLOW) {
 #define LBPC_SPF(q, ex, ey, ez, op)                                                      \
         *reinterpret_cast<VF*>(fd + (size_t)q * N + n0) = PRF::enc(f0[q], f1[q], fshift(k, q));
@@ -1013,14 +897,7 @@ LBPC_HD void step_pair_pull(const Args& a, int x0, int y, int z, const TF<P>* fs
     }
     LBPC_Q7(LBPC_SPG)
 #undef LBPC_SPG
-    double h0n = excess_minus<Mode<P>::G>(e0, g0), h1n = excess_minus<Mode<P>::G>(e1, g1);
-    if constexpr (SG::kGrid) {  // residuals of the populations leaving through the x walls
-        if (xwall) {
-            if (iso0) h0n -= wall_out<Mode<P>::G>(a, 0, y, z, out0, g0[2]);
-            if (iso1) h1n -= wall_out<Mode<P>::G>(a, 1, y, z, out1, g1[1]);
-        }
-    }
-    *reinterpret_cast<double2*>(hp + n0) = make_double2(h0n, h1n);
+    *reinterpret_cast<double2*>(hp + n0) = make_double2(excess_minus<Mode<P>::G>(e0, g0), excess_minus<Mode<P>::G>(e1, g1));
 }
 
 
@@ -1043,8 +920,7 @@ LBPC_HD void opaque(T& v) {
 // f*_q goes to slot q at x + e_q (slot qbar at x behind a wall), with the wall rules of the
 // per-node path.  Each thread reads and writes the same set of slots, so in place is safe.
 template <int P, int FLOW, bool ODD>
-LBPC_HD void step_pair_aa(const Args& a, int x0, int y, int z, TF<P>* F, TG<P>* G, double* hp,
-                          bool xwall = false) {
+LBPC_HD void step_pair_aa(const Args& a, int x0, int y, int z, TF<P>* F, TG<P>* G, double* hp) {
     using SF = Store<Mode<P>::F>;
     using SG = Store<Mode<P>::G>;
     using TFt = typename SF::T;
@@ -1061,9 +937,6 @@ LBPC_HD void step_pair_aa(const Args& a, int x0, int y, int z, TF<P>* F, TG<P>* 
     const int n0 = x0 + a.nx * (y + a.ny * z), n1 = n0 + 1;
     const bool xlo = x0 == 0, xhi = x0 + 1 == a.nx - 1;
     const bool wlo = xlo && a.wall[0], whi = xhi && a.wall[1];
-    const bool iso0 = wlo && a.wall_iso[0], iso1 = whi && a.wall_iso[1];
-    const bool wwarp = !SG::kGrid || xwall;  // 16-bit g: wall work only in wall warps
-    C lo0 = C(0), lo1 = C(0);  // wall remainders of the incoming g (16-bit g)
     const int dn0 = xlo ? n0 + a.nx - 1 : n0 - 1;      // x-neighbour x0 - 1 (wrapped)
     const int up1 = xhi ? n1 - (a.nx - 1) : n1 + 1;    // x-neighbour x1 + 1 (wrapped)
     C f0[19], f1[19], g0[7], g1[7];
@@ -1102,13 +975,13 @@ LBPC_HD void step_pair_aa(const Args& a, int x0, int y, int z, TF<P>* F, TG<P>* 
                 PRG::dec(*reinterpret_cast<const VG*>(sw + n0 + oyz), k.gshift, g0[q], g1[q]); \
             } else if constexpr ((ex) == 1) {                                           \
                 C v = SG::dec(sw[wlo ? ((q) - (op)) * N32 + n0 : dn0 + oyz], k.gshift);  \
-                if (wwarp && iso0) v = wall_in<Mode<P>::G>(a, k, 0, x0, y, z, v, lo0);  \
+                if (wlo && a.wall_iso[0]) v = SG::grid(-v + abb_source(a, k, 0, x0, y, z)); \
                 g0[q] = v;                                                              \
                 g1[q] = SG::dec(sw[n0 + oyz], k.gshift);                                    \
             } else {                                                                    \
                 g0[q] = SG::dec(sw[n1 + oyz], k.gshift);                                    \
                 C v = SG::dec(sw[whi ? ((q) - (op)) * N32 + n1 : up1 + oyz], k.gshift);  \
-                if (wwarp && iso1) v = wall_in<Mode<P>::G>(a, k, 1, x0 + 1, y, z, v, lo1); \
+                if (whi && a.wall_iso[1]) v = SG::grid(-v + abb_source(a, k, 1, x0 + 1, y, z)); \
                 g1[q] = v;                                                              \
             }                                                                           \
         }                                                                               \
@@ -1116,19 +989,8 @@ LBPC_HD void step_pair_aa(const Args& a, int x0, int y, int z, TF<P>* F, TG<P>* 
     LBPC_Q7(LBPC_AGG)
 #undef LBPC_AGG
     const double2 ep = *reinterpret_cast<const double2*>(hp + n0);
-    double e0 = excess_plus<Mode<P>::G>(ep.x, g0), e1 = excess_plus<Mode<P>::G>(ep.y, g1);
-    if constexpr (SG::kGrid) {  // the wall remainders (16-bit g): exact FP64 additions
-        if (xwall) {
-            if constexpr (!ODD) {  // natural layout: the incoming populations' own residuals
-                if (iso0) lo0 = a.wres[0][y + a.ny * z];
-                if (iso1) lo1 = a.wres[1][y + a.ny * z];
-            }
-            if (iso0) { e0 += f2d_exact(lo0); g0[1] += lo0; }
-            if (iso1) { e1 += f2d_exact(lo1); g1[2] += lo1; }
-        }
-    }
+    const double e0 = excess_plus<Mode<P>::G>(ep.x, g0), e1 = excess_plus<Mode<P>::G>(ep.y, g1);
     pair_collide<P, FLOW>(a, f0, f1, g0, g1, e0, e1);
-    const C out0 = g0[2], out1 = g1[1];  // populations leaving through the x walls
     // fresh copies of the indices and bases for the scatter (see opaque())
     int m0 = n0, mdn = dn0, mup = up1, tsy = sy, tsz = sz;
     TF<P>* Fw = F;
@@ -1175,14 +1037,16 @@ LBPC_HD void step_pair_aa(const Args& a, int x0, int y, int z, TF<P>* F, TG<P>* 
                 const TGt v0 = SG::enc_g(g0[q], k.gshift), v1 = SG::enc_g(g1[q], k.gshift); \
                 dq[(m0 + 1) + o2] = v0;                                                 \
                 TGt vb = v1;                                                            \
-                if (wwarp && iso1) vb = wall_in_aa<Mode<P>::G>(a, k, 1, x0 + 1, y, z, out1, v1); \
+                if (whi && a.wall_iso[1])                                               \
+                    vb = SG::enc_g(-SG::dec(v1, k.gshift) + abb_source(a, k, 1, x0 + 1, y, z), k.gshift); \
                 dq[whi ? ((op) - (q)) * N32 + (m0 + 1) : mup + o2] = vb;                \
                 g0[q] = SG::dec(v0, k.gshift);                                          \
                 g1[q] = SG::dec(v1, k.gshift);                                          \
             } else {                                                                    \
                 const TGt v0 = SG::enc_g(g0[q], k.gshift), v1 = SG::enc_g(g1[q], k.gshift); \
                 TGt vb = v0;                                                            \
-                if (wwarp && iso0) vb = wall_in_aa<Mode<P>::G>(a, k, 0, x0, y, z, out0, v0); \
+                if (wlo && a.wall_iso[0])                                               \
+                    vb = SG::enc_g(-SG::dec(v0, k.gshift) + abb_source(a, k, 0, x0, y, z), k.gshift); \
                 dq[wlo ? ((op) - (q)) * N32 + m0 : mdn + o2] = vb;                      \
                 dq[m0 + o2] = v1;                                                       \
                 g0[q] = SG::dec(v0, k.gshift);                                          \
@@ -1192,19 +1056,8 @@ LBPC_HD void step_pair_aa(const Args& a, int x0, int y, int z, TF<P>* F, TG<P>* 
     }
     LBPC_Q7(LBPC_ASG)
 #undef LBPC_ASG
-    double h0n = excess_minus<Mode<P>::G>(e0, g0), h1n = excess_minus<Mode<P>::G>(e1, g1);
-    if constexpr (SG::kGrid) {  // residuals of the populations leaving through the x walls
-        if (xwall) {
-            if constexpr (ODD) {  // (the incoming values' residuals are in wres already)
-                if (iso0) h0n -= f2d_exact(out0 - g0[2]);
-                if (iso1) h1n -= f2d_exact(out1 - g1[1]);
-            } else {
-                if (iso0) h0n -= wall_out<Mode<P>::G>(a, 0, y, z, out0, g0[2]);
-                if (iso1) h1n -= wall_out<Mode<P>::G>(a, 1, y, z, out1, g1[1]);
-            }
-        }
-    }
-    *reinterpret_cast<double2*>(hp + n0) = make_double2(h0n, h1n);
+    *reinterpret_cast<double2*>(hp + n0) =
+        make_double2(excess_minus<Mode<P>::G>(e0, g0), excess_minus<Mode<P>::G>(e1, g1));
 }
 
 // Macroscopic state of node n and its contributions to the diagnostics sums
@@ -1217,10 +1070,10 @@ LBPC_HD void macro_node(const Args& a, int n, const TF<P>* fs,
     const Coef<C>& k = coef<C>(a);
     const int x = n % a.nx, y = (n / a.nx) % a.ny, z = n / (a.nx * a.ny);
     const Nb b = make_nb(a, x, y, z);
-    C f[19], g[7], lo[7] = {};
+    C f[19], g[7];
     if constexpr (FLOW) gather_f<Mode<P>::F, LAYOUT, true>(a, b, n, fs, f);
-    gather_g<Mode<P>::G, LAYOUT, true>(a, b, n, x, y, z, gs, g, lo);
-    const double e = add_lo<Mode<P>::G>(excess_plus<Mode<P>::G>(hp[n], g), lo, 1.0);
+    gather_g<Mode<P>::G, LAYOUT, true>(a, b, n, x, y, z, gs, g);
+    const double e = excess_plus<Mode<P>::G>(hp[n], g);
     const double h = a.hs + e;
     double Td, fld;  // reported: the FP64 inversion
     invert_excess(a, e, Td, fld);
@@ -1243,9 +1096,7 @@ LBPC_HD void macro_node(const Args& a, int n, const TF<P>* fs,
         acc[2] += (double)rho;
         if (x == 0) {
             const double Tw = a.Tw[0][y + a.ny * z];
-            if (a.wall_iso[0])
-                acc[3] += 2.0 * ((double)g[1] + (double)lo[1] + (double)k.gshift) -
-                          (double)k.wT_cref * Tw;
+            if (a.wall_iso[0]) acc[3] += 2.0 * ((double)g[1] + (double)k.gshift) - (double)k.wT_cref * Tw;
             acc[4] += (Tw - Td) * 2.0;
         }
         const C gsum = ((g[1] + g[2]) + (g[3] + g[4])) + (g[5] + g[6]);
@@ -1301,30 +1152,19 @@ LBPC_HD void init_node(const Args& a, int x, int y, int z, const double* Qf, con
     }
 #define LBPC_IG(q, ex, ey, ez, op)                                                       \
     {                                                                                   \
-        using SG = Store<Mode<P>::G>;                                                   \
         double v;                                                                       \
-        int rface = -1; /* face whose residual this slot carries (16-bit g) */          \
-        if constexpr (LAYOUT == LAYOUT_AA_NATURAL) {                                    \
-            v = state_g(a, k, Qg, h0, q, n);                                            \
-            if (b.template wall<ex, ey, ez>() && a.wall_iso[q - 1]) rface = q - 1;      \
-        } else {                                                                        \
-            const bool w = b.template wall<-(ex), -(ey), -(ez)>();                      \
+        if constexpr (LAYOUT == LAYOUT_AA_NATURAL) v = state_g(a, k, Qg, h0, q, n);     \
+        else {                                                                          \
+            const bool w = b.template wall<-(ex), -(ey), -(ez)>();                             \
             if (w) {                                                                    \
                 v = state_g(a, k, Qg, h0, op, n);                                       \
-                if (a.wall_iso[op - 1]) {                                               \
+                if (a.wall_iso[op - 1])                                                 \
                     v = (double)k.wT_cref * a.Tw[op - 1][face_index(a, op - 1, x, y, z)] - v; \
-                    rface = op - 1;                                                     \
-                }                                                                       \
             } else {                                                                    \
-                v = state_g(a, k, Qg, h0, q, n + b.template off<-(ex), -(ey), -(ez)>()); \
+                v = state_g(a, k, Qg, h0, q, n + b.template off<-(ex), -(ey), -(ez)>());       \
             }                                                                           \
         }                                                                               \
-        const C r = (C)(v - (double)k.gshift);                                          \
-        const auto st = SG::enc_g(r, C(0));                                             \
-        gd[(size_t)(q - 1) * N + n] = st;                                               \
-        if constexpr (SG::kGrid) {                                                      \
-            if (rface >= 0) a.wres[rface][face_index(a, rface, x, y, z)] = r - SG::dec(st, C(0)); \
-        }                                                                               \
+        gd[(size_t)(q - 1) * N + n] = Store<Mode<P>::G>::enc_g((C)(v - (double)k.gshift), C(0)); \
     }
     LBPC_Q7(LBPC_IG)
 #undef LBPC_IG
@@ -1344,9 +1184,9 @@ LBPC_HD void init_hprime_node(const Args& a, int x, int y, int z, const double* 
     } else {
         h = h0[n];
     }
-    C g[7], lo[7] = {};
-    gather_g<Mode<P>::G, LAYOUT, true>(a, b, n, x, y, z, gs, g, lo);
-    hp[n] = add_lo<Mode<P>::G>(excess_minus<Mode<P>::G>(h - a.hs, g), lo, -1.0);
+    C g[7];
+    gather_g<Mode<P>::G, LAYOUT, true>(a, b, n, x, y, z, gs, g);
+    hp[n] = excess_minus<Mode<P>::G>(h - a.hs, g);
 }
 
 // Pre-collision populations of node (x, y, z) in FP64 (g_0 = h' = h_s + e').
@@ -1358,11 +1198,11 @@ LBPC_HD void dist_node(const Args& a, int x, int y, int z, const TF<P>* fs,
     const Nb b = make_nb(a, x, y, z);
     const size_t N = (size_t)a.N;
     const Coef<C>& k = coef<C>(a);
-    C g[7], lo[7] = {};
-    gather_g<Mode<P>::G, LAYOUT, true>(a, b, n, x, y, z, gs, g, lo);
+    C g[7];
+    gather_g<Mode<P>::G, LAYOUT, true>(a, b, n, x, y, z, gs, g);
     const double gs_ = (double)k.gshift;
     Qg[n] = a.hs + hp[n] - 6.0 * gs_;
-    for (int q = 1; q < 7; q++) Qg[(size_t)q * N + n] = ((double)g[q] + (double)lo[q]) + gs_;
+    for (int q = 1; q < 7; q++) Qg[(size_t)q * N + n] = (double)g[q] + gs_;
     if constexpr (FLOW) {
         if (Qf) {
             C f[19];
@@ -1585,9 +1425,9 @@ LBPC_HD CT<P> adj_seed_node(const Args& a, int x, int y, int z,
     const Coef<C>& k = coef<C>(a);
     const int n = x + a.nx * (y + a.ny * z);
     const Nb b = make_nb(a, x, y, z);
-    C g[7], lo[7] = {};
-    gather_g<Mode<P>::G, LAYOUT_PULL, true>(a, b, n, x, y, z, gs, g, lo);
-    const double e = add_lo<Mode<P>::G>(excess_plus<Mode<P>::G>(hp[n], g), lo, 1.0);
+    C g[7];
+    gather_g<Mode<P>::G, LAYOUT_PULL, true>(a, b, n, x, y, z, gs, g);
+    const double e = excess_plus<Mode<P>::G>(hp[n], g);
     C T, fl, dTde, dfde, dTdL, dfdL;
     invert_excess_d(k, tape_excess(a, e, C(0)), T, fl, dTde, dfde, dTdL, dfdL);
     const size_t N = (size_t)a.N;
@@ -1752,11 +1592,6 @@ LBPC_HD CT<P> adj_reverse_pair(const Args& a, int x0, int y, int z, const CT<P>*
     const int z = blockIdx.z;                                                           \
     if (x >= a.nx || y >= a.ny) return;
 
-// Whether the node pair (x0, x0 + 1) of a valid lane touches an isothermal x wall.
-__device__ __forceinline__ bool xwall_lane(const Args& a, int x0, bool valid) {
-    return valid && ((x0 == 0 && a.wall_iso[0]) || (x0 + 2 == a.nx && a.wall_iso[1]));
-}
-
 // One node per thread; with TAPE (pull) also the adjoint tape.
 template <int P, int KIND, int FLOW, bool TAPE>
 __global__ void __launch_bounds__(STEP_THREADS)
@@ -1783,10 +1618,9 @@ k_step_pull_x2(const __grid_constant__ Args a, const TF<P>* fs,
     const bool valid = x0 < a.nx && y < a.ny;
     const bool inner = !valid || (y > 0 && y < a.ny - 1 && z > 0 && z < a.nz - 1);
     const bool paired = __all_sync(0xffffffffu, inner);
-    const bool xwall = Store<Mode<P>::G>::kGrid && __any_sync(0xffffffffu, xwall_lane(a, x0, valid));
     if (!valid) return;
     if (paired) {
-        step_pair_pull<P, FLOW, TAPE>(a, x0, y, z, fs, fd, gs, gd, hp, tape_e, tape_m, xwall);
+        step_pair_pull<P, FLOW, TAPE>(a, x0, y, z, fs, fd, gs, gd, hp, tape_e, tape_m);
     } else {
         step_node<P, STEP_PULL, FLOW, TAPE>(a, x0, y, z, fs, fd, gs, gd, hp, tape_e, tape_m);
         step_node<P, STEP_PULL, FLOW, TAPE>(a, x0 + 1, y, z, fs, fd, gs, gd, hp, tape_e, tape_m);
@@ -1805,11 +1639,10 @@ k_step_aa_x2(const __grid_constant__ Args a, TF<P>* F, TG<P>* G, double* __restr
     const bool valid = x0 < a.nx && y < a.ny;
     const bool inner = !valid || (y > 0 && y < a.ny - 1 && z > 0 && z < a.nz - 1);
     const bool paired = __all_sync(0xffffffffu, inner);
-    const bool xwall = Store<Mode<P>::G>::kGrid && __any_sync(0xffffffffu, xwall_lane(a, x0, valid));
     if (!valid) return;
     constexpr int KIND = ODD ? STEP_AA_ODD : STEP_AA_EVEN;
     if (paired) {
-        step_pair_aa<P, FLOW, ODD>(a, x0, y, z, F, G, hp, xwall);
+        step_pair_aa<P, FLOW, ODD>(a, x0, y, z, F, G, hp);
     } else {
         step_node<P, KIND, FLOW>(a, x0, y, z, F, F, G, G, hp);
         step_node<P, KIND, FLOW>(a, x0 + 1, y, z, F, F, G, G, hp);
