@@ -119,8 +119,11 @@ inline void fill_coef(Coef<C>& c, const lbpc_params& p, const Derived& d) {
     c.s_nu = (C)d.s_nu;
     c.s_pi = (C)d.s_pi;
     c.s_t = (C)d.s_t;
-    const bool gshifted = p.precision == LBPC_FP16S || p.precision == LBPC_BF16S;
-    const bool shifted = gshifted || p.precision == LBPC_FP16S_G32 || p.precision == LBPC_BF16S_G32;
+    // every mode but FP64 stores (and collides) the deviations of the populations from
+    // their rest values: f - w_a and g_a - (omega_T / 2) Cp_ref Tref; in FP32 this keeps
+    // the rounding of the stored values and of the moment sums (rho - 1 instead of rho)
+    // relative to the deviations, not to the O(1) populations
+    const bool shifted = p.precision != LBPC_FP64, gshifted = shifted;
     c.fshift0 = (C)(shifted ? 1.0 / 3.0 : 0.0);
     c.fshift1 = (C)(shifted ? 1.0 / 18.0 : 0.0);
     c.fshift2 = (C)(shifted ? 1.0 / 36.0 : 0.0);
@@ -198,8 +201,6 @@ inline void fill_args(Args& a, int nx, int ny, int nz, const lbpc_params& p, con
     a.flow = p.flow_model != LBPC_FLOW_NONE;
     a.hs = d.hs;
     a.L = d.L;
-    std::memcpy(&a.Lbits, &d.L, sizeof a.Lbits);
-    a.L_below = std::nextafter((float)d.L, 0.0f);
     fill_coef(a.cf, p, d);
     fill_coef(a.cd, p, d);
 }

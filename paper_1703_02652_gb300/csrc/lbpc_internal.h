@@ -46,8 +46,6 @@ struct Args {
     const double* Tw[6]; // per-face wall temperature fields (device)
     int flow;            // flow lattice present
     double hs, L;        // FP64 copies for the enthalpy inversion
-    long long Lbits;     // bits of L as a signed integer (branch tests of the inversion)
-    float L_below;       // largest float below (float)L (mushy values on the FP32 tape)
     Coef<float> cf;
     Coef<double> cd;
 };

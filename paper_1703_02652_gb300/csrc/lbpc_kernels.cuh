@@ -93,35 +93,29 @@ LBPC_HD double f2d_exact(float v) {
     return (float)v == 0.0f || std::fabs(v) < 1.17549435e-38f ? 0.0 : (double)v;
 #endif
 }
-// double -> float rounded to nearest (ties to even) by integer operations, off the FP64
-// pipe: half an ulp of the result is added to the magnitude (less one unless the kept
-// last bit is odd) and the exponent is rebiased.  Results below 2^-126 become signed
-// zero; NaN stays NaN, values beyond the float range become infinities.
-LBPC_HD float d2f_rn(double v) {
+// double -> float rounded to nearest (ties away from zero) by integer operations, off the
+// FP64 pipe: the magnitude is truncated to the float's 23 mantissa bits and the first
+// dropped bit is added (a carry into the exponent is the correct rounding).  Results below
+// 2^-126 become signed zero (or the smallest subnormal); the inputs are finite enthalpy
+// excesses.  (A ties-to-even version with a 64-bit rounding add, and the hardware
+// conversion, both measured slower in the 16-bit step kernel.)
 #if defined(__CUDA_ARCH__)
+__device__ __forceinline__ float d2f_trunc(double v) {
     const unsigned long long u = (unsigned long long)__double_as_longlong(v);
-    const unsigned long long mag = u & 0x7fffffffffffffffull;
+    const int ex = (int)((u >> 52) & 0x7ff) - 896;  // float biased exponent
     const unsigned sign = (unsigned)(u >> 63) << 31;
-    const unsigned long long r = mag + 0x0fffffffull + ((mag >> 29) & 1ull);
-    const int ex = (int)(r >> 52) - 896;  // float biased exponent
     if (ex <= 0) return __uint_as_float(sign);
-    if (ex >= 255)
-        return __uint_as_float(sign | (mag > 0x7ff0000000000000ull ? 0x7fc00000u : 0x7f800000u));
-    return __uint_as_float(sign | (unsigned)((r >> 29) - (896ull << 23)));
+    if (ex >= 255) return __uint_as_float(sign | 0x7f800000u);
+    return __uint_as_float(sign | ((unsigned)ex << 23) | (unsigned)((u >> 29) & 0x7fffffu));
+}
+#endif
+LBPC_HD float d2f_near(double v) {
+#if defined(__CUDA_ARCH__)
+    return __uint_as_float(__float_as_uint(d2f_trunc(v)) +
+                           ((unsigned)(__double_as_longlong(v) >> 28) & 1u));
 #else
     if (std::fabs(v) < 1.1754943508222875e-38) return std::signbit(v) ? -0.0f : 0.0f;
     return (float)v;
-#endif
-}
-// Bits of a double as a signed integer: for a positive bound B, v <= 0 and v >= B (v not
-// NaN) are the integer tests bits(v) <= 0 and bits(v) >= bits(B).
-LBPC_HD long long dbits(double v) {
-#if defined(__CUDA_ARCH__)
-    return __double_as_longlong(v);
-#else
-    long long b;
-    std::memcpy(&b, &v, sizeof b);
-    return b;
 #endif
 }
 
@@ -418,12 +412,13 @@ LBPC_HD void scatter_g(const Args& a, const NB& b, int n, int x, int y, int z,
 // Eq. 2 inverted (h = C_p T + f_l L; solid for h <= h_s, liquid for h >= h_s + L, mushy
 // at T_m in between) from the FP64 enthalpy excess e = h - h_s that the rest channel
 // carries, so that the cancelling subtraction near the melting point is exact.  FP64
-// storage computes everything in FP64, and so do the reported fields and diagnostics in
-// every mode.  For the FP32 collision of the 32/16-bit modes the branch is still decided
-// on the FP64 excess, exactly, by integer tests on its bits (off the FP64 pipe); the value
-// is formed in FP32 from e rounded once to nearest: T_m + d / C_p,s, T_m + (d - L) / C_p,l
-// or d / L with d = rn(e), which is within half an FP32 ulp of e (over C_p) of the FP64
-// value (an FP64 fused multiply-add per node here cost 5% of the 16-bit step's throughput).
+// storage inverts in FP64, and so do the reported fields and diagnostics in every mode.
+// The FP32 collision of the 32/16-bit modes inverts d = e rounded once to nearest (by
+// integer operations, off the FP64 pipe): branch and value within half an FP32 ulp of e
+// of the FP64 inversion; the branch can differ from the exact one only for e within half
+// an ulp of 0 or L, where both branches give the same T and f_l to that accuracy.  (Exact
+// branch tests on the bits of e measured 2% slower on the 16-bit step, an FP64 fused
+// multiply-add for the value 5%.)
 LBPC_HD void invert_excess(const Args& a, double e, double& T, double& fl) {
     const Coef<double>& k = a.cd;
     if (e <= 0.0) {
@@ -438,24 +433,25 @@ LBPC_HD void invert_excess(const Args& a, double e, double& T, double& fl) {
     }
 }
 LBPC_HD void invert_excess(const Args& a, double e, float& T, float& fl) {
-    const long long b = dbits(e);
-    const bool solid = b <= 0, liquid = b >= a.Lbits;
-    const float d = d2f_rn(e);
     const Coef<float>& k = a.cf;
-    T = solid ? k.Tm + d * k.Cps_inv : (liquid ? k.Tm + (d - k.L) * k.Cpl_inv : k.Tm);
-    fl = solid ? 0.0f : (liquid ? 1.0f : fminf(d * k.L_inv, 1.0f));
+    const float d = d2f_near(e);
+    if (d <= 0.0f) {
+        fl = 0.0f;
+        T = k.Tm + d * k.Cps_inv;
+    } else if (d >= k.L) {
+        fl = 1.0f;
+        T = k.Tm + (d - k.L) * k.Cpl_inv;
+    } else {
+        fl = fminf(d * k.L_inv, 1.0f);
+        T = k.Tm;
+    }
 }
 
-// The excess taped for the adjoint, in the compute precision: e itself (FP64), or e
-// rounded to nearest and kept strictly inside (0, L) on the mushy branch, so that the
-// reverse sweep's branch tests in FP32 take the branch the forward took in FP64.
+// The excess taped for the adjoint, in the compute precision: exactly the value the
+// forward inversion used (e itself for FP64, e rounded to nearest otherwise), so that the
+// reverse sweep takes the forward's branch.
 LBPC_HD double tape_excess(const Args&, double e, double) { return e; }
-LBPC_HD float tape_excess(const Args& a, double e, float) {
-    const long long b = dbits(e);
-    const float r = d2f_rn(e);
-    if (b > 0 && b < a.Lbits) return fminf(fmaxf(r, 1.17549435e-38f), a.L_below);
-    return r;
-}
+LBPC_HD float tape_excess(const Args&, double e, float) { return d2f_near(e); }
 
 // Velocity factor phi of the solid closure, u = phi u*, F_s = -2 (1 - phi) rho0 u*: the
 // liquid fraction itself, or with the enthalpy-porosity drag D = A (1 - f_l)^2 / (f_l^3 +

