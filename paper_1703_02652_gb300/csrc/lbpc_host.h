@@ -119,11 +119,14 @@ inline void fill_coef(Coef<C>& c, const lbpc_params& p, const Derived& d) {
     c.s_nu = (C)d.s_nu;
     c.s_pi = (C)d.s_pi;
     c.s_t = (C)d.s_t;
-    // every mode but FP64 stores (and collides) the deviations of the populations from
-    // their rest values: f - w_a and g_a - (omega_T / 2) Cp_ref Tref; in FP32 this keeps
-    // the rounding of the stored values and of the moment sums (rho - 1 instead of rho)
-    // relative to the deviations, not to the O(1) populations
-    const bool shifted = p.precision != LBPC_FP64, gshifted = shifted;
+    // every mode but FP64 stores (and collides) the deviations f - w_a of the flow
+    // populations from their rest weights: in FP32 too, this keeps the rounding of the
+    // stored values and of the moment sums (rho - 1 instead of rho) relative to the
+    // deviations, not to O(1) populations.  16-bit g is stored as g_a - (omega_T / 2) Cp_ref
+    // Tref (16-bit range); FP32 g is not shifted: near T_m = 0, where most of a melting
+    // domain sits, the unshifted values keep their full relative precision
+    const bool shifted = p.precision != LBPC_FP64;
+    const bool gshifted = p.precision == LBPC_FP16S || p.precision == LBPC_BF16S;
     c.fshift0 = (C)(shifted ? 1.0 / 3.0 : 0.0);
     c.fshift1 = (C)(shifted ? 1.0 / 18.0 : 0.0);
     c.fshift2 = (C)(shifted ? 1.0 / 36.0 : 0.0);
