@@ -51,10 +51,11 @@ enum { LBPC_ENTH_MRT = 1, LBPC_ENTH_SRT = 2 };
  * FP32 registers otherwise.  h' and the reductions are FP64 in every mode, h - h_s is
  * formed in FP64, and the H -> (T, f_l) inversion of Eq. 2 reports FP64 fields; the FP32
  * collision inverts h - h_s rounded once to nearest (within half an FP32 ulp of the FP64
- * inversion).  Every mode but FP64 stores the deviations f - w_a and g_a - (omega_T/2)
- * Cp_ref Tref: FP32 as such (216 B per node update), FP16S / BF16S in 16 bits (116 B);
- * the _G32 modes store f in 16 bits and g in FP32 (140 B), which keeps the enthalpy
- * populations and the wall fluxes they carry at FP32 resolution. */
+ * inversion).  Every mode but FP64 stores the flow populations as deviations f - w_a:
+ * FP32 as such with g in FP32 (216 B per node update); FP16S / BF16S in 16 bits together
+ * with g_a - (omega_T/2) Cp_ref Tref (116 B); the _G32 modes store f in 16 bits and g in
+ * FP32 (140 B), which keeps the enthalpy populations and the wall fluxes they carry at
+ * FP32 resolution. */
 enum { LBPC_FP64 = 0, LBPC_FP32 = 1, LBPC_FP16S = 2, LBPC_BF16S = 3, LBPC_FP16S_G32 = 4,
        LBPC_BF16S_G32 = 5 };
 enum { LBPC_PULL = 0, LBPC_AA = 1 };
