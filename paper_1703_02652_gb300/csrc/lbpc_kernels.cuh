@@ -1216,6 +1216,13 @@ LBPC_HD void dist_node(const Args& a, int x, int y, int z, const TF<P>* fs,
 // forward inversion used; rho, j), which fixes every nonlinear factor.
 // ---------------------------------------------------------------------------------
 
+// Contribution of the adjoint la of an anti-bounce-back population to dJ/dT_w of its wall
+// node: omega_T Cp_ref la.  FP64 for FP64 storage; otherwise the FP32 product converted
+// exactly by integer operations (the sum over steps stays FP64 without FP64-pipe products
+// in the sweep, where the wall lanes' code is predicated in every warp).
+LBPC_HD double wall_grad(const Coef<double>& k, double la) { return k.wT_cref * la; }
+LBPC_HD double wall_grad(const Coef<float>& k, float la) { return f2d_exact(k.wT_cref * la); }
+
 // Derivatives of the Eq. 2 inversion on the branch the forward took.
 template <class C>
 LBPC_HD void invert_excess_d(const Coef<C>& k, C d, C& T, C& fl, C& dTde, C& dfde, C& dTdL,
@@ -1468,7 +1475,7 @@ LBPC_HD CT<P> adj_reverse_node(const Args& a, const NB& b, int x, int y, int z,
             if (a.wall_iso[op - 1]) {                                                   \
                 lg[q] = -la;                                                            \
                 if (op - 1 == wface)                                                    \
-                    gtw[face_index(a, op - 1, x, y, z)] += (double)k.wT_cref * (double)la; \
+                    gtw[face_index(a, op - 1, x, y, z)] += wall_grad(k, la);            \
             } else {                                                                    \
                 lg[q] = la;                                                             \
             }                                                                           \
@@ -1546,12 +1553,12 @@ LBPC_HD CT<P> adj_reverse_pair(const Args& a, int x0, int y, int z, const CT<P>*
             const C la = ld_any<true>(pl + (whi ? ((op) - (q)) * N32 + n1 : up1 + o));  \
             const bool iso = whi && a.wall_iso[1];                                      \
             lg1[q] = iso ? -la : la;                                                    \
-            if (iso && wface == 1) gtw[y + a.ny * z] += (double)k.wT_cref * (double)la; \
+            if (iso && wface == 1) gtw[y + a.ny * z] += wall_grad(k, la);          \
         } else {                                                                        \
             const C la = ld_any<true>(pl + (wlo ? ((op) - (q)) * N32 + n0 : dn0 + o));  \
             const bool iso = wlo && a.wall_iso[0];                                      \
             lg0[q] = iso ? -la : la;                                                    \
-            if (iso && wface == 0) gtw[y + a.ny * z] += (double)k.wT_cref * (double)la; \
+            if (iso && wface == 0) gtw[y + a.ny * z] += wall_grad(k, la);          \
             lg1[q] = ld_any<true>(pl + n0 + o);                                         \
         }                                                                               \
     }
