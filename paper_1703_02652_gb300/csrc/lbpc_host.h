@@ -152,6 +152,15 @@ inline void fill_coef(Coef<C>& c, const lbpc_params& p, const Derived& d) {
     c.r_nu13 = (C)(-d.s_nu / 4.0);
     c.c_nu13 = (C)((1.0 - 0.5 * d.s_nu) / 4.0);
     c.r_t = (C)(-d.s_t / 8.0);
+    c.k_e = (C)(19.0 * (1.0 - d.s_e) / 2394.0);
+    c.k_eps = (C)((1.0 - d.s_eps) / 252.0);
+    c.k_q = (C)((1.0 - d.s_q) / 40.0);
+    c.k_nu9 = (C)((1.0 - d.s_nu) / 36.0);
+    c.k_pi10 = (C)((1.0 - d.s_pi) / 72.0);
+    c.k_nu11 = (C)((1.0 - d.s_nu) / 12.0);
+    c.k_pi12 = (C)((1.0 - d.s_pi) / 24.0);
+    c.k_nu13 = (C)((1.0 - d.s_nu) / 4.0);
+    c.k_t = (C)((1.0 - d.s_t) / 8.0);
     c.sig4_6 = (C)(d.sigma4 / 6.0);  // sig4 = sig5 = sig6 (Eq. 47)
     c.sig5_6 = (C)(d.sigma4 / 6.0);
     c.sig6_4 = (C)(d.sigma4 / 4.0);
@@ -182,7 +191,15 @@ inline void fill_coef(Coef<C>& c, const lbpc_params& p, const Derived& d) {
     c.j_h_pi12 = (C)((1.0 - 0.5 * d.s_pi) / 24.0);
     c.j_s_nu13 = (C)(d.s_nu / 4.0);
     c.j_h_nu13 = (C)((1.0 - 0.5 * d.s_nu) / 4.0);
-    c.j_m_t = (C)(-d.s_t / 8.0);
+    c.j_k_e = (C)((1.0 - d.s_e) / 2394.0);
+    c.j_k_eps = (C)((1.0 - d.s_eps) / 252.0);
+    c.j_k_q = (C)((1.0 - d.s_q) / 40.0);
+    c.j_k_nu9 = (C)((1.0 - d.s_nu) / 36.0);
+    c.j_k_pi10 = (C)((1.0 - d.s_pi) / 72.0);
+    c.j_k_nu11 = (C)((1.0 - d.s_nu) / 12.0);
+    c.j_k_pi12 = (C)((1.0 - d.s_pi) / 24.0);
+    c.j_k_nu13 = (C)((1.0 - d.s_nu) / 4.0);
+    c.j_k_t = (C)((1.0 - d.s_t) / 8.0);
     c.darcy = p.darcy_A > 0;
     c.darcy_A = (C)p.darcy_A;
     c.darcy_eps = (C)(p.darcy_eps > 0 ? p.darcy_eps : 1e-3);

@@ -24,6 +24,8 @@ struct Coef {
     // r_k = -s_k / |row k|^2, c_k = (1 - s_k / 2) (FF_k prefactor) / |row k|^2
     C r_e, c_e, r_eps, c_eps, r_q, c_q, r_nu9, c_nu9, r_pi10, c_pi10, r_nu11, c_nu11, r_pi12,
         c_pi12, r_nu13, c_nu13, r_t;
+    // f* rebuilt from its moments: k_k = (1 - s_k) / |row k|^2 (row 1: times 19)
+    C k_e, k_eps, k_q, k_nu9, k_pi10, k_nu11, k_pi12, k_nu13, k_t;
     // D3Q7 relaxation: sig4 / 6, sig5 / 6, sig6 / 4, sig_chi / 2; Cp_l - Cp_s; 2 gshift
     C sig4_6, sig5_6, sig6_4, hchi, dCp, gshift2;
     // per-phase conductivities (conduction only): rates per node from f_l
@@ -33,9 +35,10 @@ struct Coef {
     int darcy;
     C darcy_A, darcy_eps;
     // adjoint of the D3Q19 relaxation: j_s_k = s_k / |row k|^2, j_h_k = (1 - s_k/2) / |row
-    // k|^2, j_m_t = -s_t / 8
+    // k|^2, j_k_k = (1 - s_k) / |row k|^2 (row 16-18: s_t)
     C j_s_e, j_h_e, j_s_eps, j_h_eps, j_s_q, j_h_q, j_s_nu9, j_h_nu9, j_s_pi10, j_h_pi10,
-        j_s_nu11, j_h_nu11, j_s_pi12, j_h_pi12, j_s_nu13, j_h_nu13, j_m_t;
+        j_s_nu11, j_h_nu11, j_s_pi12, j_h_pi12, j_s_nu13, j_h_nu13;
+    C j_k_e, j_k_eps, j_k_q, j_k_nu9, j_k_pi10, j_k_nu11, j_k_pi12, j_k_nu13, j_k_t;
 };
 
 struct Args {

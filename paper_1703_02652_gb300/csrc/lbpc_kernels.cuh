@@ -75,6 +75,8 @@ template <> struct Mode<LBPC_BF16S_G32> { static constexpr int F = LBPC_BF16S, G
 template <int P> using TF = typename Store<Mode<P>::F>::T;
 template <int P> using TG = typename Store<Mode<P>::G>::T;
 template <int P> using CT = typename Store<Mode<P>::F>::C;
+// 16-bit f: the flow collision rebuilds f* from its moments (collide_flow)
+template <int P> constexpr bool kRebuild = sizeof(TF<P>) == 2;
 
 // Exact float -> double by integer operations (subnormal floats, below 1.2e-38, become
 // zero); keeps the conversions off the FP64 pipe, which on GB300 issues a few
@@ -499,9 +501,20 @@ LBPC_HD void flow_macro(const C* f, const Coef<C>& k, C T, C fl, C& rho, C& jx,
     uz = phi * usz;
 }
 
-// D3Q19 MRT collision with forcing (Eq. 49-54) in correction form:
+// Back-transform output: f*_a itself (RB) or the correction added to f_a.
+template <bool RB, class C>
+LBPC_HD void put_f(C& f, C v) {
+    if constexpr (RB) f = v;
+    else f += v;
+}
+
+// D3Q19 MRT collision with forcing (Eq. 49-54):
 // f* = f + M^-1 [ -Lambda (m - m^eq) + (I - Lambda/2) FF ], with M^-1 = M^T diag(1/|row|^2).
-template <class C>
+// RB = false adds the correction to f.  RB = true rebuilds f* from its moments,
+// f* = M^-1 [ m - Lambda (m - m^eq) + (I - Lambda/2) FF ] (M^-1 M = I), so the 19 inputs
+// are not held to the end: fewer live registers, which lets the 16-bit pair kernels run
+// six blocks per SM (FP32 keeps the correction form, which measured faster there).
+template <bool RB, class C>
 LBPC_HD void collide_flow(C* f, const Coef<C>& k, C T, C fl, C& ux, C& uy, C& uz, C& rho_o,
                           C& jx_o, C& jy_o, C& jz_o) {
     // grouped sums: axis pairs and the xy, xz, yz diagonal quadruples
@@ -522,7 +535,8 @@ LBPC_HD void collide_flow(C* f, const Coef<C>& k, C T, C fl, C& ux, C& uy, C& uz
     const C yz_p = (f[15] - f[16]) - (f[17] - f[18]);
     const C sax = a1 + a3 + a5, sdg = sxy + sxz + syz;
 
-    const C rho = f[0] + sax + sdg + k.frho;
+    const C rst = f[0] + sax + sdg;  // rho of the stored representation
+    const C rho = rst + k.frho;
     const C tx = xy_x + xz_x, ty = xy_y + yz_y, tz = xz_z + yz_z;
     const C jx = b1 + tx, jy = b3 + ty, jz = b5 + tz;
     rho_o = rho;
@@ -552,42 +566,76 @@ LBPC_HD void collide_flow(C* f, const Coef<C>& k, C T, C fl, C& ux, C& uy, C& uz
     // equilibrium moments (Eq. 53) and forcing moments (Eq. 54), c = 1
     const C uxx = ux * ux, uyy = uy * uy, uzz = uz * uz, u2 = uxx + uyy + uzz;
     const C Fu = Fx * ux + Fy * uy + Fz * uz;
-    const C ru2 = rho * u2, rux = rho * ux, r23 = C(2.0 / 3.0) * rho;
+    const C ru2 = rho * u2, rux = rho * ux;
     const C pxx_eq = rho * (C(3) * uxx - u2), pww_eq = rho * (uyy - uzz);
     const C FFxx = C(6) * Fx * ux - C(2) * Fu, FFww = C(2) * (Fy * uy - Fz * uz);
 
-    // d_k = [-s_k (m_k - meq_k) + (1 - s_k/2) FF_k] / |row k|^2; the products of the rates,
-    // (1 - s_k/2) and 1/|row k|^2 are folded into the r_* and c_* constants on the host
-    const C d1 = k.r_e * (sdg - f[0] - ru2) + k.c_e * Fu;
-    const C d2 = k.r_eps * (C(9) * f[0] - C(7) * sax - C(2) * sdg + C(5.5) * ru2) + k.c_eps * Fu;
-    const C d3 = Fx * C(0.1), d5 = Fy * C(0.1), d7 = Fz * C(0.1);
-    const C d4 = k.r_q * (m4 + r23 * ux) + k.c_q * Fx;
-    const C d6 = k.r_q * (m6 + r23 * uy) + k.c_q * Fy;
-    const C d8 = k.r_q * (m8 + r23 * uz) + k.c_q * Fz;
-    const C d9 = k.r_nu9 * (m9 - pxx_eq) + k.c_nu9 * FFxx;
-    const C d10 = k.r_pi10 * (m10 + C(0.5) * pxx_eq) + k.c_pi10 * FFxx;
-    const C d11 = k.r_nu11 * (m11 - pww_eq) + k.c_nu11 * FFww;
-    const C d12 = k.r_pi12 * (m12 + C(0.5) * pww_eq) + k.c_pi12 * FFww;
-    const C d13 = k.r_nu13 * (xy_p - rux * uy) + k.c_nu13 * (Fx * uy + Fy * ux);
-    const C d14 = k.r_nu13 * (yz_p - rho * uy * uz) + k.c_nu13 * (Fy * uz + Fz * uy);
-    const C d15 = k.r_nu13 * (xz_p - rux * uz) + k.c_nu13 * (Fx * uz + Fz * ux);
-    const C d16 = k.r_t * m16, d17 = k.r_t * m17, d18 = k.r_t * m18;
+    // d_k = [-s_k (m_k - meq_k) + (1 - s_k/2) FF_k] / |row k|^2 (correction form), or with RB
+    // m*_k / |row k|^2 = d_k + m_k / |row k|^2 = [(1 - s_k) m_k + s_k meq_k + (1 - s_k/2)
+    // FF_k] / |row k|^2; the products of the rates, (1 - s_k/2), (1 - s_k) and 1/|row k|^2
+    // are folded into the r_*, c_* and k_* constants on the host.  With RB, rows 0-2 leave
+    // out the rest-weight moments (1, -11, 3) rho_st of the stored representation, which
+    // enter the back-transform as w_a rho_st
+    C d1, d2, d3, d4, d5, d6, d7, d8, d9, d10, d11, d12, d13, d14, d15, d16, d17, d18;
+    if constexpr (RB) {
+        const C rq23 = k.r_q * (C(2.0 / 3.0) * rho);
+        d1 = k.k_e * (sdg - f[0]) - k.r_e * ru2 + k.c_e * Fu;
+        d2 = k.k_eps * (C(9) * f[0] - C(7) * sax - C(2) * sdg) + C(5.5) * k.r_eps * ru2 +
+             k.c_eps * Fu;
+        d3 = (jx + Fx) * C(0.1), d5 = (jy + Fy) * C(0.1), d7 = (jz + Fz) * C(0.1);
+        d4 = k.k_q * m4 + rq23 * ux + k.c_q * Fx;
+        d6 = k.k_q * m6 + rq23 * uy + k.c_q * Fy;
+        d8 = k.k_q * m8 + rq23 * uz + k.c_q * Fz;
+        d9 = k.k_nu9 * m9 - k.r_nu9 * pxx_eq + k.c_nu9 * FFxx;
+        d10 = k.k_pi10 * m10 + C(0.5) * k.r_pi10 * pxx_eq + k.c_pi10 * FFxx;
+        d11 = k.k_nu11 * m11 - k.r_nu11 * pww_eq + k.c_nu11 * FFww;
+        d12 = k.k_pi12 * m12 + C(0.5) * k.r_pi12 * pww_eq + k.c_pi12 * FFww;
+        d13 = k.k_nu13 * xy_p - k.r_nu13 * (rux * uy) + k.c_nu13 * (Fx * uy + Fy * ux);
+        d14 = k.k_nu13 * yz_p - k.r_nu13 * (rho * uy * uz) + k.c_nu13 * (Fy * uz + Fz * uy);
+        d15 = k.k_nu13 * xz_p - k.r_nu13 * (rux * uz) + k.c_nu13 * (Fx * uz + Fz * ux);
+        d16 = k.k_t * m16, d17 = k.k_t * m17, d18 = k.k_t * m18;
+    } else {
+        const C r23 = C(2.0 / 3.0) * rho;
+        d1 = k.r_e * (sdg - f[0] - ru2) + k.c_e * Fu;
+        d2 = k.r_eps * (C(9) * f[0] - C(7) * sax - C(2) * sdg + C(5.5) * ru2) + k.c_eps * Fu;
+        d3 = Fx * C(0.1), d5 = Fy * C(0.1), d7 = Fz * C(0.1);
+        d4 = k.r_q * (m4 + r23 * ux) + k.c_q * Fx;
+        d6 = k.r_q * (m6 + r23 * uy) + k.c_q * Fy;
+        d8 = k.r_q * (m8 + r23 * uz) + k.c_q * Fz;
+        d9 = k.r_nu9 * (m9 - pxx_eq) + k.c_nu9 * FFxx;
+        d10 = k.r_pi10 * (m10 + C(0.5) * pxx_eq) + k.c_pi10 * FFxx;
+        d11 = k.r_nu11 * (m11 - pww_eq) + k.c_nu11 * FFww;
+        d12 = k.r_pi12 * (m12 + C(0.5) * pww_eq) + k.c_pi12 * FFww;
+        d13 = k.r_nu13 * (xy_p - rux * uy) + k.c_nu13 * (Fx * uy + Fy * ux);
+        d14 = k.r_nu13 * (yz_p - rho * uy * uz) + k.c_nu13 * (Fy * uz + Fz * uy);
+        d15 = k.r_nu13 * (xz_p - rux * uz) + k.c_nu13 * (Fx * uz + Fz * ux);
+        d16 = k.r_t * m16, d17 = k.r_t * m17, d18 = k.r_t * m18;
+    }
 
-    // back-transform: f*_a = f_a + sum_k M_ka d_k (columns of Eq. 51), with the sums shared
-    // between the members of each axis pair and diagonal quadruple
-    f[0] += C(-30) * d1 + C(12) * d2;
-    const C eax = C(-11) * d1 - C(4) * d2;
+    // back-transform: sum_k M_ka d_k (columns of Eq. 51; with RB plus w_a rho_st, as M w =
+    // (1, -11, 3, 0, ...)), with the sums shared between the members of each axis pair and
+    // diagonal quadruple
+    C e0, eax, edg;
+    if constexpr (RB) {
+        e0 = rst * C(1.0 / 3.0) + C(-30) * d1 + C(12) * d2;
+        eax = rst * C(1.0 / 18.0) + C(-11) * d1 - C(4) * d2;
+        edg = rst * C(1.0 / 36.0) + C(8) * d1 + d2;
+    } else {
+        e0 = C(-30) * d1 + C(12) * d2;
+        eax = C(-11) * d1 - C(4) * d2;
+        edg = C(8) * d1 + d2;
+    }
+    put_f<RB>(f[0], e0);
     const C ox = d3 - C(4) * d4, oy = d5 - C(4) * d6, oz = d7 - C(4) * d8;
     const C ex1 = eax + C(2) * d9 - C(4) * d10;
     const C cyz = eax - d9 + C(2) * d10, w11 = d11 - C(2) * d12;
     const C ey1 = cyz + w11, ez1 = cyz - w11;
-    f[1] += ex1 + ox;
-    f[2] += ex1 - ox;
-    f[3] += ey1 + oy;
-    f[4] += ey1 - oy;
-    f[5] += ez1 + oz;
-    f[6] += ez1 - oz;
-    const C edg = C(8) * d1 + d2;
+    put_f<RB>(f[1], ex1 + ox);
+    put_f<RB>(f[2], ex1 - ox);
+    put_f<RB>(f[3], ey1 + oy);
+    put_f<RB>(f[4], ey1 - oy);
+    put_f<RB>(f[5], ez1 + oz);
+    put_f<RB>(f[6], ez1 - oz);
     const C X = d3 + d4, Y = d5 + d6, Z = d7 + d8;
     const C a910 = edg + d9 + d10, b1112 = d11 + d12;
     const C exy = a910 + b1112, exz = a910 - b1112;
@@ -595,26 +643,26 @@ LBPC_HD void collide_flow(C* f, const Coef<C>& k, C T, C fl, C& ux, C& uy, C& uz
     {  // xy: f7..f10 = e_xy +-(d13) + (+-X +-Y) + (+-d16 -+d17)
         const C u = X + d16, v = Y - d17, P = exy + d13, Q = exy - d13;
         const C s = u + v, w = v - u;
-        f[7] += P + s;
-        f[8] += Q + w;
-        f[9] += Q - w;
-        f[10] += P - s;
+        put_f<RB>(f[7], P + s);
+        put_f<RB>(f[8], Q + w);
+        put_f<RB>(f[9], Q - w);
+        put_f<RB>(f[10], P - s);
     }
     {  // xz: f11..f14
         const C u = X - d16, v = Z + d18, P = exz + d15, Q = exz - d15;
         const C s = u + v, w = v - u;
-        f[11] += P + s;
-        f[12] += Q + w;
-        f[13] += Q - w;
-        f[14] += P - s;
+        put_f<RB>(f[11], P + s);
+        put_f<RB>(f[12], Q + w);
+        put_f<RB>(f[13], Q - w);
+        put_f<RB>(f[14], P - s);
     }
     {  // yz: f15..f18
         const C u = Y + d17, v = Z - d18, P = eyz + d14, Q = eyz - d14;
         const C s = u + v, w = v - u;
-        f[15] += P + s;
-        f[16] += Q + w;
-        f[17] += Q - w;
-        f[18] += P - s;
+        put_f<RB>(f[15], P + s);
+        put_f<RB>(f[16], Q + w);
+        put_f<RB>(f[17], Q - w);
+        put_f<RB>(f[18], P - s);
     }
 }
 
@@ -746,7 +794,8 @@ LBPC_HD void step_node(const Args& a, int x, int y, int z, const TF<P>* fs,
     invert_excess(a, e, T, fl);
     C ux = C(0), uy = C(0), uz = C(0), rho = C(0), jx = C(0), jy = C(0), jz = C(0);
     if constexpr (FLOW)  // FLOW 2: the drag closure, phi(f_l) in place of f_l
-        collide_flow(f, k, T, FLOW == 2 ? darcy_phi(k, fl) : fl, ux, uy, uz, rho, jx, jy, jz);
+        collide_flow<kRebuild<P>>(f, k, T, FLOW == 2 ? darcy_phi(k, fl) : fl, ux, uy, uz, rho, jx,
+                                  jy, jz);
     if constexpr (TAPE) {  // macroscopic tape of the pre-collision state (adjoint)
         tape_e[n] = tape_excess(a, e, C(0));
         if constexpr (FLOW) {
@@ -783,10 +832,10 @@ LBPC_HD void pair_collide(const Args& a, CT<P>* f0, CT<P>* f1, CT<P>* g0, CT<P>*
     C ux0 = C(0), uy0 = C(0), uz0 = C(0), ux1 = C(0), uy1 = C(0), uz1 = C(0);
     if constexpr (FLOW) {
         C r0, jx0, jy0, jz0, r1, jx1, jy1, jz1;
-        collide_flow(f0, k, T0, FLOW == 2 ? darcy_phi(k, fl0) : fl0, ux0, uy0, uz0, r0, jx0,
-                     jy0, jz0);
-        collide_flow(f1, k, T1, FLOW == 2 ? darcy_phi(k, fl1) : fl1, ux1, uy1, uz1, r1, jx1,
-                     jy1, jz1);
+        collide_flow<kRebuild<P>>(f0, k, T0, FLOW == 2 ? darcy_phi(k, fl0) : fl0, ux0, uy0, uz0,
+                                  r0, jx0, jy0, jz0);
+        collide_flow<kRebuild<P>>(f1, k, T1, FLOW == 2 ? darcy_phi(k, fl1) : fl1, ux1, uy1, uz1,
+                                  r1, jx1, jy1, jz1);
         if constexpr (TAPE) {
             const size_t N = (size_t)a.N;
             *reinterpret_cast<VC*>(tape_m + n0) = VC{r0, r1};
@@ -1315,6 +1364,7 @@ LBPC_HD C collide_adjoint(const Coef<C>& k, C d, C rho, C jx, C jy, C jz, C* lf,
         const C sax = a1 + a3 + a5, sdg = sxy + sxz + syz;
         // raw moments R_k = (M lambda*_f)_k; mu_k = R_k / |row k|^2 enters only through the
         // host constants j_s_k = s_k / |row k|^2 and j_h_k = (1 - s_k/2) / |row k|^2
+        const C R0 = L[0] + sax + sdg;
         const C R1 = C(-30) * L[0] - C(11) * sax + C(8) * sdg;
         const C R2 = C(12) * L[0] - C(4) * sax + sdg;
         const C tx = xy_x + xz_x, ty = xy_y + yz_y, tz = xz_z + yz_z;
@@ -1363,25 +1413,30 @@ LBPC_HD C collide_adjoint(const Coef<C>& k, C d, C rho, C jx, C jy, C jz, C* lf,
                        C(2) * (lFx * usx + lFy * usy + lFz * usz));
         const C lFb = lFz + C(0.5) * lusz;
         lT += k.gbeta * lFb;
-        // lambda_f = lambda*_f + M^T lambda_m, lambda_m = (lrho, -s mu, lj, ...), with the
-        // sums shared within axis pairs and diagonal quadruples as in the forward
-        const C d0 = lrho, d3 = lusx, d5 = lusy, d7 = lusz;
-        const C d1 = -q1, d2 = -q2, d4 = -q4, d6 = -q6, d8 = -q8;
-        const C d9 = -q9, d10 = -q10, d11 = -q11, d12 = -q12;
-        const C d13 = -q13, d14 = -q14, d15 = -q15;
-        const C d16 = k.j_m_t * R16, d17 = k.j_m_t * R17, d18 = k.j_m_t * R18;
-        lf[0] += d0 - C(30) * d1 + C(12) * d2;
+        // lambda_f = lambda*_f + M^T lambda_m, lambda_m = (lrho, -s mu, lj, ...), written as
+        // M^T (diag(1/|row|^2) R + lambda_m) (M^T diag(1/|row|^2) M = I): lambda*_f is
+        // rebuilt from its moments instead of held to the end, and the row-k coefficient
+        // (1 - s_k) / |row k|^2 comes from the host; the sums are shared within axis pairs
+        // and diagonal quadruples as in the forward
+        const C d0 = lrho + R0 * C(1.0 / 19.0), d3 = lusx + mu3, d5 = lusy + mu5, d7 = lusz + mu7;
+        const C d1 = k.j_k_e * R1, d2 = k.j_k_eps * R2, d4 = k.j_k_q * R4, d6 = k.j_k_q * R6,
+                d8 = k.j_k_q * R8;
+        const C d9 = k.j_k_nu9 * R9, d10 = k.j_k_pi10 * R10, d11 = k.j_k_nu11 * R11,
+                d12 = k.j_k_pi12 * R12;
+        const C d13 = k.j_k_nu13 * xy_p, d14 = k.j_k_nu13 * yz_p, d15 = k.j_k_nu13 * xz_p;
+        const C d16 = k.j_k_t * R16, d17 = k.j_k_t * R17, d18 = k.j_k_t * R18;
+        lf[0] = d0 - C(30) * d1 + C(12) * d2;
         const C eax = d0 - C(11) * d1 - C(4) * d2;
         const C ox = d3 - C(4) * d4, oy = d5 - C(4) * d6, oz = d7 - C(4) * d8;
         const C ex1 = eax + C(2) * d9 - C(4) * d10;
         const C cyz = eax - d9 + C(2) * d10, w1112 = d11 - C(2) * d12;
         const C ey1 = cyz + w1112, ez1 = cyz - w1112;
-        lf[1] += ex1 + ox;
-        lf[2] += ex1 - ox;
-        lf[3] += ey1 + oy;
-        lf[4] += ey1 - oy;
-        lf[5] += ez1 + oz;
-        lf[6] += ez1 - oz;
+        lf[1] = ex1 + ox;
+        lf[2] = ex1 - ox;
+        lf[3] = ey1 + oy;
+        lf[4] = ey1 - oy;
+        lf[5] = ez1 + oz;
+        lf[6] = ez1 - oz;
         const C edg = d0 + C(8) * d1 + d2;
         const C X = d3 + d4, Y = d5 + d6, Z = d7 + d8;
         const C a910 = edg + d9 + d10, b1112 = d11 + d12;
@@ -1390,26 +1445,26 @@ LBPC_HD C collide_adjoint(const Coef<C>& k, C d, C rho, C jx, C jy, C jz, C* lf,
         {
             const C u = X + d16, v = Y - d17, Pp = exy + d13, Qq = exy - d13;
             const C s = u + v, w = v - u;
-            lf[7] += Pp + s;
-            lf[8] += Qq + w;
-            lf[9] += Qq - w;
-            lf[10] += Pp - s;
+            lf[7] = Pp + s;
+            lf[8] = Qq + w;
+            lf[9] = Qq - w;
+            lf[10] = Pp - s;
         }
         {
             const C u = X - d16, v = Z + d18, Pp = exz + d15, Qq = exz - d15;
             const C s = u + v, w = v - u;
-            lf[11] += Pp + s;
-            lf[12] += Qq + w;
-            lf[13] += Qq - w;
-            lf[14] += Pp - s;
+            lf[11] = Pp + s;
+            lf[12] = Qq + w;
+            lf[13] = Qq - w;
+            lf[14] = Pp - s;
         }
         {
             const C u = Y + d17, v = Z - d18, Pp = eyz + d14, Qq = eyz - d14;
             const C s = u + v, w = v - u;
-            lf[15] += Pp + s;
-            lf[16] += Qq + w;
-            lf[17] += Qq - w;
-            lf[18] += Pp - s;
+            lf[15] = Pp + s;
+            lf[16] = Qq + w;
+            lf[17] = Qq - w;
+            lf[18] = Pp - s;
         }
     }
     le += lT * dTde + lfl * dfde;
@@ -1608,9 +1663,10 @@ k_step(const __grid_constant__ Args a, const TF<P>* fs, TF<P>* fd,
 
 // Pull step, two nodes per thread along x (even nx).  Warps whose rows all lie away
 // from the y and z faces take the paired path; others run the per-node path twice.
-// With TAPE also the adjoint tape.  Five blocks per SM (96 registers); four when taping.
+// With TAPE also the adjoint tape.  Blocks per SM: FP32 five (96 registers), four when
+// taping; 16-bit f (collision rebuilt from the moments) six (80 registers), five when taping.
 template <int P, int FLOW, bool TAPE>
-__global__ void __launch_bounds__(STEP_THREADS, TAPE ? 4 : 5)
+__global__ void __launch_bounds__(STEP_THREADS, TAPE ? (kRebuild<P> ? 5 : 4) : (kRebuild<P> ? 6 : 5))
 k_step_pull_x2(const __grid_constant__ Args a, const TF<P>* fs,
                TF<P>* fd, const TG<P>* gs, TG<P>* gd,
                double* __restrict__ hp, CT<P>* __restrict__ tape_e,
@@ -1632,9 +1688,10 @@ k_step_pull_x2(const __grid_constant__ Args a, const TF<P>* fs,
 
 
 // AA step, two nodes per thread along x (even nx); same vote as the pull pair kernel.
-// Five blocks per SM (96 registers; a few bytes of spills in some variants).
+// Five blocks per SM (96 registers; a few bytes of spills in some variants); the even step
+// with 16-bit f six (80 registers; the odd step spills at six).
 template <int P, int FLOW, bool ODD>
-__global__ void __launch_bounds__(STEP_THREADS, 5)
+__global__ void __launch_bounds__(STEP_THREADS, kRebuild<P> && !ODD ? 6 : 5)
 k_step_aa_x2(const __grid_constant__ Args a, TF<P>* F, TG<P>* G, double* __restrict__ hp) {
     const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -1809,9 +1866,10 @@ k_adj_reverse(const __grid_constant__ Args a, const CT<P>* __restrict__ lin,
     if (((threadIdx.x + blockDim.x * threadIdx.y) & 31) == 0) Lpart[warp_slot()] += (double)w;
 }
 
-// Reverse step, two nodes per thread along x (even nx); the pull kernels' vote.
+// Reverse step, two nodes per thread along x (even nx); the pull kernels' vote.  Five
+// blocks per SM (96 registers, no spills).
 template <int P, bool FLOW>
-__global__ void __launch_bounds__(STEP_THREADS, 4)
+__global__ void __launch_bounds__(STEP_THREADS, 5)
 k_adj_reverse_x2(const __grid_constant__ Args a, const CT<P>* __restrict__ lin,
                  CT<P>* __restrict__ lout, const CT<P>* __restrict__ tape_e,
                  const CT<P>* __restrict__ tape_m, int wface, double* gtw,
