@@ -13,9 +13,14 @@ below 1e-6 on every quantity, so the errors below are those of the arithmetic, a
 is held to the larger of its bound and three times that drift.
 
 Bounds (relative, final point): FP32 storage 1e-3 on every quantity (the stated bound);
-16-bit f with FP32 g 1e-3 on liquid fraction and melt depth; pure FP16 1e-2 and BF16 (both
-BF16 modes) 5e-2 on liquid fraction and melt depth.  The 16-bit flow populations miss the
-stated 1e-3 on Nu and on the f_l = 1/2 crossing over 50k steps; those are reported only.
+16-bit f with FP32 g 1e-3 on liquid fraction and melt depth at Pr 50 and 5e-3 at Pr 0.02;
+pure FP16 1e-2 and BF16 (both BF16 modes) 5e-2 on liquid fraction and melt depth.  The
+16-bit flow populations miss the stated 1e-3 on Nu and on the f_l = 1/2 crossing over 50k
+steps; those are reported only.  At Pr 0.02 the 50k-step error of every 16-bit-f mode
+depends on the realization of its rounding: a 1e-7 perturbation of the initial enthalpy,
+which moves the FP64 run by 3e-7, moves the FP16 f + FP32 g liquid fraction by 7e-4 to
+2.5e-3, so that mode's error there (measured 4.2e-4 and 1.7e-3 on two builds whose stored
+values differ only at FP32 rounding ties) gets a bound above that spread.
 
 Run with LBPC_LONG=1 (and LBPC_LONG_OUT=<file> to keep the per-point errors as JSON).
 """
@@ -36,12 +41,12 @@ pytestmark = [pytest.mark.gpu,
 STEPS = 50000
 KEYS = ("liquid_vol", "front_mean", "front_mid", "nu_hot", "nu_fd")
 _DEPTH = ("liquid_vol", "front_mean")
-BOUND = {
-    inp.FP32: dict.fromkeys(KEYS, 1e-3),
-    inp.FP16_G32: dict.fromkeys(_DEPTH, 1e-3),
-    inp.BF16_G32: dict.fromkeys(_DEPTH, 5e-2),
-    inp.FP16: dict.fromkeys(_DEPTH, 1e-2),
-    inp.BF16: dict.fromkeys(_DEPTH, 5e-2),
+BOUND = {  # precision -> Pr -> quantity -> bound
+    inp.FP32: {0.02: dict.fromkeys(KEYS, 1e-3), 50.0: dict.fromkeys(KEYS, 1e-3)},
+    inp.FP16_G32: {0.02: dict.fromkeys(_DEPTH, 5e-3), 50.0: dict.fromkeys(_DEPTH, 1e-3)},
+    inp.BF16_G32: {0.02: dict.fromkeys(_DEPTH, 5e-2), 50.0: dict.fromkeys(_DEPTH, 5e-2)},
+    inp.FP16: {0.02: dict.fromkeys(_DEPTH, 1e-2), 50.0: dict.fromkeys(_DEPTH, 1e-2)},
+    inp.BF16: {0.02: dict.fromkeys(_DEPTH, 5e-2), 50.0: dict.fromkeys(_DEPTH, 5e-2)},
 }
 
 
@@ -83,7 +88,8 @@ def test_full_length_precision_sweep(Pr):
     print(f"Pr={Pr} fp64 drift (1e-7 initial perturbation): " + ", ".join(
         f"{k} {drift[k][-1]:.2e}" for k in KEYS))
     failures = []
-    for prec, bounds in BOUND.items():
+    for prec, by_pr in BOUND.items():
+        bounds = by_pr[Pr]
         H = _history(Pr, prec)
         assert H["nan"].max() == 0
         rec = {}
